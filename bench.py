@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the DOT hot path on GB300: forward and forward+backward Mrays/s.
+
+Workload (N = 1): the NeRF-synthetic-shaped scene (depth-9 octree, 2.9 M leaves, SH degree 3,
+FP16 leaves, FP32 arithmetic) seen by 100 cameras of 800x800 on a radius-4 hemisphere (focal
+1111).  One step renders all 100 views in one launch (64 M rays).  Extra keys: forward+backward
+on 2^16-ray batches from those views, the refine pass (signal, selection, prune/sample), the
+roofline of the forward kernel, the FP64 CPU oracle on a bounded sample, and end-to-end
+throughput through host buffers.  Multi-GPU: every rank renders its own copy of the workload
+(weak scaling; the only collectives are the barrier and the max of the timings).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd & fwd+bwd at 800² SH-deg3; serve p50/p99 ms vs plain launch"
+WORKLOAD = "nerf_synthetic_d9_sh3_f16_100x800x800"
+BATCH = 1 << 16
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="dot", choices=["dot", "reference"])
+    p.add_argument("--views", type=int, default=100)
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200", "-i",
+                                       str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------------------------
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2307_15333_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and workload, if the
+    kernel sources are unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"csrc_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != csrc_hash():
+        return None
+    return float(m.group(1))
+
+
+def oracle_baseline(scene, cams, budget_s: float, threads: int):
+    """The FP64 oracle as it stands, timed on the host cores over a strided pixel sample."""
+    import oracle
+    import seeded_inputs as si
+    t = oracle.scene_tree(scene)
+    sig, sh = si.leaf_params(t["leaf_key"], t["leaf_inside"], scene)
+    s64, h64 = si.storage_to_f64(sig, scene.storage), si.storage_to_f64(sh, scene.storage)
+    lo, size = oracle.root_of(scene)
+    W, H = cams[0].width, cams[0].height
+    # calibrate on a small sample, then size the measured sample to the time budget
+    stride = 4093
+    pix = np.arange(0, W * H, stride)
+    o, d = si.camera_rays(cams[0], pix)
+    t0 = time.perf_counter()
+    oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    rate = len(pix) / dt
+    n_views = min(len(cams), 10)
+    want = max(1000, int(rate * budget_s))
+    stride = max(1, (W * H * n_views) // want)
+    os_, ds_ = [], []
+    for v in range(n_views):
+        p = np.arange(v % stride, W * H, stride)
+        o, d = si.camera_rays(cams[v], p)
+        os_.append(o)
+        ds_.append(d)
+    o, d = np.concatenate(os_), np.concatenate(ds_)
+    t0 = time.perf_counter()
+    oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": o.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+            "sample": f"every {stride}th pixel of the first {n_views} 800x800 views "
+                      f"({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ----------------------------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import seeded_inputs as si
+    scene, cams = si.config_nerf_synthetic(args.views)
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = oracle_baseline(scene, cams, per_step, threads)
+        if i >= args.warmup:
+            vals.append(b)
+    v = statistics.median([b["value"] for b in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------------------------
+# the GB300 arm
+# ----------------------------------------------------------------------------------------------
+def run_dot(args):
+    import torch
+    import torch.distributed as tdist
+
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.render import render_views
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    scene, cams = si.config_nerf_synthetic(args.views)
+    W, H = cams[0].width, cams[0].height
+    tree = dot.octree_from_scene(scene)
+    L = tree.n_leaves
+    cam_t = dot.cameras_tensor(cams)
+    rays = dot.rays_cameras(cam_t, W, H)
+    R = len(cams) * W * H
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    rgb = torch.empty(R, 3, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # algorithmic bytes of one launch (counting pass, not timed)
+    st = dot.dot_render_stats(tree, rays, opts)
+    bs = 2                                                # FP16 storage
+    K = scene.n_coeffs
+    P = (1 + 3 * K) * bs                                  # leaf payload of an occupied segment
+    seg, occ = st["segments"], st["occupied"]
+    alg_bytes = occ * P + (seg - occ) * bs + seg * 4 + R * 12
+
+    # ---- forward: W warm-up steps, K timed steps, one launch each ----
+    for _ in range(args.warmup):
+        dot.dot_render_forward(tree, rays, opts, rgb)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for a, b in ev:
+        a.record(stream)
+        dot.dot_render_forward(tree, rays, opts, rgb)
+        b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    total_ms = max_over_ranks(total_ms)
+    value = R * args.steps * ws / (total_ms / 1e3) / 1e6
+    mean_launch_s = statistics.mean(launch_ms) / 1e3
+    assert tree.status() == 0
+
+    # ---- forward + backward on 2^16-ray batches (fixed synthetic dL/dC) ----
+    nb = 8
+    batches = []
+    for i in range(nb):
+        o, d = si.ray_batch(cams, BATCH, seed=7000 + i)
+        batches.append(dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()))
+    g = torch.from_numpy(np.random.default_rng(1).normal(0, 1e-3, (BATCH, 3)).astype(np.float32)).cuda()
+    brgb = torch.empty(BATCH, 3, device="cuda")
+    gs = torch.zeros(L, device="cuda")
+    gsh = torch.zeros(L, 3, K, device="cuda")
+    pairs = max(50, 5 * args.steps)
+    for i in range(3 * nb):
+        r = batches[i % nb]
+        dot.dot_render_forward(tree, r, opts, brgb)
+        dot.dot_render_backward(tree, r, opts, g, brgb, gs, gsh)
+    torch.cuda.synchronize()
+    barrier()
+    clocks2 = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(pairs):
+        r = batches[i % nb]
+        dot.dot_render_forward(tree, r, opts, brgb)
+        dot.dot_render_backward(tree, r, opts, g, brgb, gs, gsh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk2 = clocks2.stop()
+    fb_ms = max_over_ranks(e0.elapsed_time(e1))
+    fwd_bwd = {"value": BATCH * pairs * ws / (fb_ms / 1e3) / 1e6, "unit": "Mrays/s",
+               "batch_rays": BATCH, "pairs": pairs, "ms_per_pair": fb_ms / pairs,
+               "grad": "fixed synthetic dL/dC; FP32 gradients accumulate across pairs",
+               "clocks": clk2}
+
+    # ---- end to end through host buffers (pinned cameras in, pinned images out) ----
+    cams_host = cam_t.cpu().pin_memory()
+    out_host = torch.empty(len(cams), H, W, 3, dtype=torch.float32, pin_memory=True)
+    render_views(tree, cams_host, W, H, opts, out_host)
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        render_views(tree, cams_host, W, H, opts, out_host)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": R * e2e_steps * ws / e2e_s / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": int(cams_host.numel() * 4),
+           "d2h_bytes_per_step": int(out_host.numel() * 4)}
+
+    # ---- refine pass (signal, selection, prune / sample), once, on the resident tree ----
+    sig = torch.zeros(L, device="cuda")
+    pm = torch.empty(L, dtype=torch.uint8, device="cuda")
+    sm = torch.empty(L, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in batches:
+        dot.dot_accumulate_signal(tree, r, opts, dot.dot.DOT_SIGNAL_MAX_WEIGHT, sig)
+    dot.dot_select_masks(tree, sig, dot.select_opts(dot.dot.DOT_SELECT_FRACTION, 0.2,
+                                                    dot.dot.DOT_SELECT_FRACTION, 0.05), pm, sm)
+    counts = dot.dot_refine_plan(tree, pm, sm, 11)
+    lm = torch.empty(counts["n_leaves"], dtype=torch.int32, device="cuda")
+    dot.dot_refine_prune(tree, pm, sm, 11, lm)
+    torch.cuda.synchronize()
+    refine_ms = (time.perf_counter() - t0) * 1e3
+    refine = {"ms": refine_ms, "leaves_before": L, "leaves_after": counts["n_leaves"],
+              "signal": f"MAX_WEIGHT over {nb} x 2^16 rays", "select": "bottom 20% / top 5%"}
+
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / mean_launch_s / 1e9
+    traffic = profiled_traffic("render_fwd_nerf_synthetic_800")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "march_kernel<__half,16,kFwd,false>",
+                "alg_bytes_per_launch": alg_bytes,
+                "per_unit": {"occupied_segment_B": P + 4, "empty_segment_B": bs + 4,
+                             "ray_output_B": 12},
+                "segments_per_ray": seg / R, "occupied_per_ray": occ / R}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(scene, cams, args.cpu_seconds, os.cpu_count() or 1)
+
+    line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "leaves": L, "nodes": tree.n_nodes,
+                       "views": len(cams), "width": W, "height": H, "rays_per_step": R,
+                       "sh_degree": scene.sh_degree, "leaf_storage": "f16",
+                       "l2": "inputs larger than L2, no flush: leaves %.0f MB + nodes %.0f MB "
+                             "vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6),
+                       "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine,
+            "wall_s_timed": t_wall}
+    if rank == 0:
+        print(json.dumps(line))
+    tree.free()
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dot(args)
+
+
+if __name__ == "__main__":
+    main()

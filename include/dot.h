@@ -1,0 +1,313 @@
+/*
+ * dot.h -- C ABI of the GB300 Dynamic PlenOctree (DOT) hot path.
+ *
+ * The library renders rays through a sparse octree whose leaves hold a density sigma and
+ * degree-0..3 real spherical-harmonic colour coefficients (Sec. 3, Preliminaries, Eq. 1-2),
+ * differentiates that render, accumulates the per-leaf training signal of Sec. 3.1, selects
+ * leaves by threshold or rank (Sec. 3.2, Algorithm 1), and restructures the tree by the prune
+ * (Eq. 3) and sample (Eq. 4) operations.  Every call runs hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every call
+ *  - Every call returns an int status: DOT_OK (0) or a negative DOT_ERR_* code; the message of
+ *    the last failure on the calling thread is returned by dot_last_error().
+ *  - Argument errors (null pointers, sizes out of range, unsupported degrees or modes) are
+ *    detected on the host before any launch; nothing is launched then and outputs are untouched.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *    asynchronous on it unless stated otherwise.
+ *  - Device pointers passed in are owned by the caller; the library never frees them.  The
+ *    library owns the opaque dot_tree and the arrays it holds; those are allocated through the
+ *    caller's dot_allocator when one is given, else with cudaMallocAsync on the call's stream.
+ *  - Anomalies seen inside kernels (a ray exceeding the step cap) set bits of a per-tree device
+ *    status word, read and cleared by dot_tree_status().
+ *
+ * Geometry
+ *  - The root cube is [c - h, c + h]^3 (world units).  A cell at level l (root = 0) with
+ *    integer corner k covers [k, k + 1) * 2^-l of the root in each axis.  Levels go up to 16.
+ *  - Keys: key = (1 << 3l) | interleave(kx, ky, kz) with x the most significant bit of each
+ *    triple; the child in slot j = 4 bx + 2 by + bz of a cell has key (key << 3) | j.
+ *  - Child table child[n][8]: >= 0 internal node id, < 0 leaf id v stored as -1 - v.  Node 0 is
+ *    the root; the root is always internal.
+ *  - Leaf parameters: sigma[L] and sh[L][row] in the storage type, where a row holds the SH
+ *    coefficients [3 channels][K] (K = (degree + 1)^2) padded to a multiple of 16 bytes
+ *    (row = sh_row_stride elements).  Colour c = act(sum_k sh[ch][k] Y_k(d)) with the real SH
+ *    basis Y_k evaluated at the unit ray direction d; density max(sigma, 0).
+ */
+#ifndef DOT_H
+#define DOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOT_OK 0
+#define DOT_ERR_INVALID_ARG (-1)
+#define DOT_ERR_OOM (-2)
+#define DOT_ERR_CUDA (-3)
+#define DOT_ERR_STEP_LIMIT (-4)
+#define DOT_ERR_UNSUPPORTED (-5)
+
+#define DOT_STORAGE_F32 0
+#define DOT_STORAGE_F16 1
+#define DOT_STORAGE_BF16 2
+
+#define DOT_PRIM_SPHERE 0   /* p = (cx, cy, cz, r) */
+#define DOT_PRIM_BOX 1      /* p = (lox, loy, loz, hix, hiy, hiz) */
+#define DOT_PRIM_CYLINDER 2 /* p = (cx, cz, r, y0, y1): axis along +y */
+
+#define DOT_ACT_SIGMOID 0
+#define DOT_ACT_LINEAR 1
+
+#define DOT_SIGNAL_NONE 0
+#define DOT_SIGNAL_SUM_ALPHA 1  /* S_v += 1 - exp(-sigma delta) over every segment in v (Sec. 3.1) */
+#define DOT_SIGNAL_MAX_WEIGHT 2 /* S_v = max(S_v, T alpha) */
+#define DOT_SIGNAL_SIGMA 3      /* S_v = max(sigma_v, 0) (the density signal of Sec. 3.1) */
+
+#define DOT_SELECT_NONE 0
+#define DOT_SELECT_THRESHOLD 1 /* prune: S <= value; sample: S > value (Sec. 3.2) */
+#define DOT_SELECT_FRACTION 2  /* prune: ceil(value L) smallest by (S asc, id asc);
+                                  sample: ceil(value L) largest by (S desc, id asc) (Algorithm 1) */
+
+#define DOT_MERGE_MEAN 0
+#define DOT_MERGE_SUM 1
+#define DOT_MERGE_MAX 2
+
+#define DOT_RAYS_BUFFER 0
+#define DOT_RAYS_CAMERAS 1
+
+#define DOT_PRECISION_AUTO 0  /* F32 storage -> exact-t, 16-bit storage -> fast */
+#define DOT_PRECISION_FAST 1  /* float32 plane times and fast exponentials */
+#define DOT_PRECISION_EXACT 2 /* float-float plane times and full-precision exponentials */
+
+#define DOT_STATUS_STEP_LIMIT 1u /* a ray hit the step cap; its output is truncated */
+
+typedef struct dot_tree dot_tree;
+
+/* Caller-supplied allocator for the arrays the tree owns.  alloc returns NULL on failure. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+} dot_allocator;
+
+/* One primitive; parameters are integers in units of 2^-24 of the root edge, measured from the
+ * root's low corner (the layout of an int64 [n][8] array). */
+typedef struct {
+    int64_t type;
+    int64_t p[7];
+} dot_primitive;
+
+typedef struct {
+    float center[3];
+    float half_size;
+    int32_t max_depth;  /* D, 1..16 */
+    int32_t sh_degree;  /* 0..3 */
+    int32_t storage;    /* DOT_STORAGE_* */
+    int32_t n_primitives;
+    const dot_primitive *primitives; /* HOST pointer, n_primitives entries (<= 4096) */
+    float density_lo, density_hi;    /* sigma ~ U(lo, hi) in finest cells meeting the scene */
+    float sh_std, sh_dc;             /* SH ~ N(0, std) (Irwin-Hall n = 4), DC term + dc */
+    uint64_t seed;
+} dot_build_desc;
+
+typedef struct {
+    int64_t n_nodes, n_leaves;
+    int32_t max_level;     /* deepest level holding a leaf */
+    int32_t sh_degree;
+    int32_t n_coeffs;      /* K */
+    int32_t storage;
+    int32_t sh_row_stride; /* elements per SH row (>= 3K, row bytes a multiple of 16) */
+    int32_t pad_;
+    float center[3];
+    float half_size;
+    int32_t *child;        /* device [n_nodes][8] */
+    int32_t *node_parent;  /* device [n_nodes] (-1 for the root) */
+    uint64_t *node_key;    /* device [n_nodes] */
+    int32_t *leaf_parent;  /* device [n_leaves] */
+    uint64_t *leaf_key;    /* device [n_leaves] */
+    void *sigma;           /* device [n_leaves], storage type */
+    void *sh;              /* device [n_leaves][sh_row_stride], storage type */
+} dot_tree_info;
+
+/* Host copy of a tree (checkpoint / import).  sh is [n_leaves][3K] without row padding. */
+typedef struct {
+    int64_t n_nodes, n_leaves;
+    int32_t sh_degree, storage;
+    float center[3];
+    float half_size;
+    const int32_t *child;
+    const int32_t *node_parent;
+    const uint64_t *node_key;
+    const int32_t *leaf_parent;
+    const uint64_t *leaf_key;
+    const void *sigma;
+    const void *sh;
+} dot_host_tree;
+
+/* Pinhole camera: c2w row-major 3x4 (columns right, up, back, position); looks down -z.
+ * Pixel (i, j) (column, row from the top) has the ray built by these float32 round-to-nearest
+ * operations: xc = ((i + .5) - cx) / fx, yc = -(((j + .5) - cy) / fy),
+ * e_a = ((R[a][0] xc) + (R[a][1] yc)) - R[a][2], d = e * (1 / sqrt((e0 e0 + e1 e1) + e2 e2)). */
+typedef struct {
+    float c2w[12];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} dot_camera;
+
+typedef struct {
+    int32_t kind;      /* DOT_RAYS_BUFFER or DOT_RAYS_CAMERAS */
+    int32_t n_cameras; /* CAMERAS */
+    const dot_camera *cameras; /* CAMERAS: device [n_cameras] */
+    int32_t width, height;     /* CAMERAS: shared by every camera; ray id = (cam H + j) W + i */
+    int64_t n_rays;            /* BUFFER */
+    const float *origins;      /* BUFFER: device [n_rays][3] */
+    const float *dirs;         /* BUFFER: device [n_rays][3], unit length */
+} dot_rays;
+
+typedef struct {
+    float background[3];  /* added as T_final * background */
+    float eps_T;          /* stop after the segment that takes T below eps_T; 0 disables; < 1 */
+    int32_t color_act;    /* DOT_ACT_* */
+    int32_t signal_mode;  /* fused signal in render calls: NONE, SUM_ALPHA or MAX_WEIGHT */
+    int32_t precision;    /* DOT_PRECISION_* */
+    int32_t max_steps;    /* per-ray cell-step cap; 0 = 3 * 2^max_level + 64 */
+} dot_render_opts;
+
+typedef struct {
+    int32_t prune_mode;  /* DOT_SELECT_* */
+    int32_t sample_mode;
+    double prune_value;  /* tau, or the fraction of leaves */
+    double sample_value; /* gamma, or the fraction of leaves */
+} dot_select_opts;
+
+typedef struct {
+    int64_t n_nodes, n_leaves;  /* after the refine */
+    int64_t n_pruned_groups;    /* parents merged (Eq. 3) */
+    int64_t n_sampled;          /* leaves subdivided (Eq. 4) */
+    int64_t n_capped;           /* sample marks ignored at the depth cap */
+} dot_refine_counts;
+
+/* A per-leaf FP32 array carried through a refine: dst[new][width] from src[old][width]. */
+typedef struct {
+    const float *src;
+    float *dst;
+    int32_t width;
+    int32_t merge; /* DOT_MERGE_*: how the 8 children of a merged parent combine */
+} dot_leaf_array;
+
+/* Message of the last failure on this thread ("" if none). */
+const char *dot_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int dot_version(void);
+
+/*
+ * dot_octree_build -- the octree of the primitive union (Sec. 3 Preliminaries: POT's octree,
+ * here carved from seeded primitives in place of a trained NeRF-SH, Sec. 4.1).
+ * The root is always subdivided; a cell is subdivided while its open interior meets a primitive
+ * (integer-exact tests) and its level is below max_depth.  Numbering is canonical: nodes and
+ * leaves each in breadth-first order, by Morton key within a level.  Leaves at max_depth meeting
+ * the scene get sigma ~ U(density_lo, density_hi), others sigma = 0; every leaf gets SH
+ * coefficients; values are drawn by SplitMix64(seed) at counter 64 key + component and rounded
+ * to the storage type.  Synchronises the stream once per level.  *out receives a new tree.
+ */
+int dot_octree_build(const dot_build_desc *desc, const dot_allocator *alloc, void *stream,
+                     dot_tree **out);
+
+/* Frees the tree and its arrays (stream-ordered on the stream of the last call). */
+int dot_tree_free(dot_tree *tree);
+
+/* Sizes and device pointers of the tree (valid until the next refine or free). */
+int dot_tree_get_info(const dot_tree *tree, dot_tree_info *info);
+
+/* Copies the tree to host buffers sized from dot_tree_get_info (sh without row padding: [L][3K]).
+ * Any pointer may be NULL to skip that array.  Synchronises the stream. */
+int dot_tree_export(const dot_tree *tree, void *stream, int32_t *child, int32_t *node_parent,
+                    uint64_t *node_key, int32_t *leaf_parent, uint64_t *leaf_key, void *sigma,
+                    void *sh);
+
+/* Creates a tree from host arrays after checking that they describe a valid octree (child
+ * pointers in range, each node and leaf referenced once, keys consistent with parents). */
+int dot_tree_import(const dot_host_tree *host, const dot_allocator *alloc, void *stream,
+                    dot_tree **out);
+
+/* Synchronises the stream, returns the tree's device status bits (DOT_STATUS_*) and clears
+ * them. */
+int dot_tree_status(dot_tree *tree, void *stream, uint32_t *status);
+
+/*
+ * dot_render_forward -- Eq. 1-2 per ray: the ray's segments through the leaves in order,
+ * alpha_i = 1 - exp(-max(sigma,0) delta_i), w_i = T_i alpha_i, C = sum_i w_i c_i + T bg,
+ * stopping after the segment that takes T below eps_T.
+ * rgb: device [R][3] float (written); T_final: device [R] or NULL; signal: device [L] or NULL,
+ * accumulated with opts->signal_mode (the caller initialises it).
+ */
+int dot_render_forward(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
+                       float *rgb, float *T_final, float *signal, void *stream);
+
+/*
+ * dot_render_backward -- gradient of L = sum_r grad_rgb[r] . rgb[r] with respect to the leaf
+ * parameters, by recomputing each ray's march (no per-sample state from the forward):
+ *   dL/dsh[v][ch][k] += g_ch w_i act'(z_ch) Y_k,
+ *   dL/dsigma[v]     += [sigma_v > 0] delta_i sum_ch g_ch (T_{i+1} c_ch - (C_ch - C_{<=i,ch})).
+ * grad_rgb, rgb: device [R][3] (rgb = this tree's forward output for the same rays and opts);
+ * grad_sigma: device [L] float (+=); grad_sh: device [L][3][K] float (+=); signal as forward.
+ */
+int dot_render_backward(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
+                        const float *grad_rgb, const float *rgb, float *grad_sigma,
+                        float *grad_sh, float *signal, void *stream);
+
+/*
+ * dot_accumulate_signal -- the per-leaf training signal of Sec. 3.1 (Algorithm 1, optimization
+ * step): SUM_ALPHA or MAX_WEIGHT by marching the rays (densities only), or SIGMA (no rays).
+ * signal: device [L] float, accumulated (SIGMA: written).
+ */
+int dot_accumulate_signal(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
+                          int32_t mode, float *signal, void *stream);
+
+/*
+ * dot_select_masks -- prune and sample marks from the signal (Sec. 3.2; Algorithm 1 pruning
+ * and sampling).  Rank selections break ties by leaf id.  signal: device [L] float;
+ * prune_mark, sample_mark: device [L] uint8 (written 0/1).
+ */
+int dot_select_masks(const dot_tree *tree, const float *signal, const dot_select_opts *opts,
+                     uint8_t *prune_mark, uint8_t *sample_mark, void *stream);
+
+/*
+ * dot_refine_plan -- the sizes dot_refine_prune will produce for these marks (synchronises).
+ */
+int dot_refine_plan(const dot_tree *tree, const uint8_t *prune_mark, const uint8_t *sample_mark,
+                    int32_t depth_cap, dot_refine_counts *out, void *stream);
+
+/*
+ * dot_refine_prune -- applies prune (Eq. 3) and sample (Eq. 4) in place on the tree.
+ *  - A parent other than the root whose 8 children are leaves, all prune-marked and none
+ *    sample-marked, becomes a leaf holding their mean (pairwise FP32 sum x 1/8, rounded to the
+ *    storage type).
+ *  - A sample-marked leaf above depth_cap becomes an internal node with 8 leaf children holding
+ *    exact copies of its values.
+ *  - New numbering: leaves = survivors (old order), merged parents (old node order), children of
+ *    sampled leaves (old leaf order x slot); nodes = surviving nodes (old order), then the
+ *    sampled leaves (old leaf order).
+ * leaf_map: device [n_leaves after] int32 (written): the old leaf id, or -1 - old parent id for
+ * merged leaves.  aux[n_aux]: extra per-leaf arrays remapped the same way (dst sized by the
+ * plan).  Frees the old arrays; previous dot_tree_get_info pointers become invalid.
+ */
+int dot_refine_prune(dot_tree *tree, const uint8_t *prune_mark, const uint8_t *sample_mark,
+                     int32_t depth_cap, int32_t *leaf_map, const dot_leaf_array *aux,
+                     int32_t n_aux, void *stream);
+
+/*
+ * dot_render_stats -- counts of the march for these rays (not part of any hot path): out[0] =
+ * rays entering the root, out[1] = segments (cell steps), out[2] = occupied segments
+ * (sigma > 0, delta > 0), out[3] = child-table loads.  Synchronises the stream.
+ */
+int dot_render_stats(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
+                     int64_t out[4], void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOT_H */

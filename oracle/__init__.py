@@ -78,7 +78,7 @@ def lib():
             L.oracle_segments.restype = ctypes.c_int64
             L.oracle_sh_basis.argtypes = [ctypes.c_int32, P, P]
             L.oracle_render.argtypes = [ctypes.POINTER(_OTree), ctypes.POINTER(_OOpts), P, P,
-                                        ctypes.c_int64, P, P, P, P, P, ctypes.c_int32, P,
+                                        ctypes.c_int64, P, P, P, P, P, ctypes.c_int32, P, P,
                                         ctypes.c_int32]
             L.oracle_backward.argtypes = [ctypes.POINTER(_OTree), ctypes.POINTER(_OOpts), P, P,
                                           ctypes.c_int64, P, P, P, P, P, P, P]
@@ -182,9 +182,10 @@ def sh_basis(deg: int, d) -> np.ndarray:
 
 def render(tree, root_lo, root_size, sigma, sh, sh_degree, o, d, *, bg=(1.0, 1.0, 1.0),
            eps_T=1e-4, color_act=ACT_SIGMOID, signal=None, signal_mode=SIGNAL_NONE,
-           threads=1):
+           threads=1, margin=False):
     """Eq. 1-2 per ray.  sigma [L] and sh [L,3,K] are float64 copies of the stored values.
-    Returns rgb [n,3], T_final [n], segments used per ray [n]; `signal` is accumulated in place."""
+    Returns rgb [n,3], T_final [n], segments used per ray [n] (and, with margin=True, each ray's
+    closest relative approach of T to eps_T); `signal` is accumulated in place."""
     L = lib()
     ot, keep = _as_otree(tree)
     op = _opts(root_lo, root_size, sh_degree, color_act, bg, eps_T)
@@ -196,11 +197,14 @@ def render(tree, root_lo, root_size, sigma, sh, sh_degree, o, d, *, bg=(1.0, 1.0
     rgb = np.zeros((n, 3), np.float64)
     Tf = np.zeros(n, np.float64)
     nseg = np.zeros(n, np.int32)
+    mg = np.zeros(n, np.float64)
     if signal is not None:
         assert signal.dtype == np.float64 and signal.flags.c_contiguous
     L.oracle_render(ctypes.byref(ot), ctypes.byref(op), _ptr(sigma), _ptr(sh), n, _ptr(o),
                     _ptr(d), _ptr(rgb), _ptr(Tf), _ptr(signal) if signal is not None else None,
-                    int(signal_mode), _ptr(nseg), int(threads))
+                    int(signal_mode), _ptr(nseg), _ptr(mg), int(threads))
+    if margin:
+        return rgb, Tf, nseg, mg
     return rgb, Tf, nseg
 
 

@@ -300,13 +300,14 @@ static void leaf_color(const oopts *op, const double *sh, int32_t v, const doubl
 
 static void render_one(const otree *t, const oopts *op, const double *sigma, const double *sh,
                        const float *of, const float *df, double rgb[3], double *Tf,
-                       double *signal, int32_t signal_mode, int32_t *nseg) {
+                       double *signal, int32_t signal_mode, int32_t *nseg, double *margin) {
     segvec v = {0};
     ray_segments(t, op, of, df, &v);
     double dir[3] = {df[0], df[1], df[2]};
     double Y[16], z[3], c[3];
     oracle_sh_basis(op->sh_degree, dir, Y);
     double T = 1.0, C[3] = {0, 0, 0};
+    double mg = INFINITY; /* closest approach of T_{i+1} to eps_T, relative to eps_T */
     int64_t i;
     for (i = 0; i < v.n; i++) {
         int32_t leaf = v.s[i].leaf;
@@ -321,21 +322,27 @@ static void render_one(const otree *t, const oopts *op, const double *sigma, con
             else if (signal_mode == 2 && w > signal[leaf]) signal[leaf] = w;
         }
         T = T * (1.0 - alpha);
-        if (op->eps_T > 0.0 && T < op->eps_T) { i++; break; }
+        if (op->eps_T > 0.0) {
+            double m = fabs(T - op->eps_T) / op->eps_T;
+            if (m < mg) mg = m;
+            if (T < op->eps_T) { i++; break; }
+        }
     }
     for (int ch = 0; ch < 3; ch++) rgb[ch] = C[ch] + T * op->bg[ch];
     *Tf = T;
     if (nseg) *nseg = (int32_t)i;
+    if (margin) *margin = mg;
     free(v.s);
 }
 
 int oracle_render(const otree *t, const oopts *op, const double *sigma, const double *sh,
                   int64_t n_rays, const float *o, const float *d, double *rgb, double *T_final,
-                  double *signal, int32_t signal_mode, int32_t *n_seg, int32_t n_threads) {
+                  double *signal, int32_t signal_mode, int32_t *n_seg, double *margin,
+                  int32_t n_threads) {
     if (signal) { /* the signal is a shared accumulator: plain serial loop */
         for (int64_t r = 0; r < n_rays; r++)
             render_one(t, op, sigma, sh, o + 3 * r, d + 3 * r, rgb + 3 * r, T_final + r, signal,
-                       signal_mode, n_seg ? n_seg + r : 0);
+                       signal_mode, n_seg ? n_seg + r : 0, margin ? margin + r : 0);
         return 0;
     }
 #ifdef _OPENMP
@@ -343,7 +350,7 @@ int oracle_render(const otree *t, const oopts *op, const double *sigma, const do
 #endif
     for (int64_t r = 0; r < n_rays; r++)
         render_one(t, op, sigma, sh, o + 3 * r, d + 3 * r, rgb + 3 * r, T_final + r, 0, 0,
-                   n_seg ? n_seg + r : 0);
+                   n_seg ? n_seg + r : 0, margin ? margin + r : 0);
     (void)n_threads;
     return 0;
 }

@@ -45,10 +45,13 @@ int64_t oracle_segments(const otree *t, const oopts *op, const float *o, const f
 void oracle_sh_basis(int32_t deg, const double *d, double *Y);
 
 /* forward render (Eq. 1-2).  sigma [L], sh [L][3][K] raw (pre-activation) values.
- * signal (nullable): accumulated in place with mode 1 = sum of alpha, 2 = max of weight. */
+ * signal (nullable): accumulated in place with mode 1 = sum of alpha, 2 = max of weight.
+ * margin (nullable): per ray, min over segments of |T_{i+1} - eps_T| / eps_T (infinity when
+ * eps_T = 0): how close the early-termination decision came to going the other way. */
 int oracle_render(const otree *t, const oopts *op, const double *sigma, const double *sh,
                   int64_t n_rays, const float *o, const float *d, double *rgb, double *T_final,
-                  double *signal, int32_t signal_mode, int32_t *n_seg, int32_t n_threads);
+                  double *signal, int32_t signal_mode, int32_t *n_seg, double *margin,
+                  int32_t n_threads);
 
 /* gradient of sum(grad_rgb . rgb) with respect to sigma and sh, accumulated (+=) in place;
  * abs_sigma / abs_sh (nullable) accumulate the magnitudes of the summed terms. */

@@ -1,0 +1,558 @@
+// api.cu -- the extern "C" entry points of libdot (include/dot.h): argument checks on the host,
+// tree lifecycle, import / export, and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "tree.cuh"
+
+struct dot_tree {
+    int device = 0;
+    dot::DevAlloc alloc;
+    dot::TreeArrays a;
+    float center[3] = {0, 0, 0};
+    float half_size = 1.f;
+    uint32_t *status = nullptr;
+};
+
+namespace dot {
+cudaError_t launch_march_fwd(int storage, int deg, bool exact, const TreeView &tv,
+                             const RaySource &rs, const RenderParams &rp, const RenderIO &io,
+                             cudaStream_t stream);
+cudaError_t launch_march_bwd(int storage, int deg, bool exact, const TreeView &tv,
+                             const RaySource &rs, const RenderParams &rp, const RenderIO &io,
+                             cudaStream_t stream);
+cudaError_t launch_march_signal(int storage, bool exact, const TreeView &tv, const RaySource &rs,
+                                const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
+cudaError_t launch_march_stats(int storage, bool exact, const TreeView &tv, const RaySource &rs,
+                               const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
+}  // namespace dot
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    cudaGetLastError();
+    g_err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? DOT_ERR_OOM : DOT_ERR_CUDA;
+}
+
+#define API_CK(call, where)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);   \
+    } while (0)
+
+cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+int check_tree(const dot_tree *t) {
+    if (!t) return fail(DOT_ERR_INVALID_ARG, "tree is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    if (dev != t->device) return fail(DOT_ERR_INVALID_ARG, "the current device is not the tree's device");
+    return DOT_OK;
+}
+
+int make_alloc(const dot_allocator *alloc, dot::DevAlloc &out) {
+    if (alloc) {
+        if (!alloc->alloc || !alloc->free)
+            return fail(DOT_ERR_INVALID_ARG, "allocator needs both alloc and free");
+        out.user = *alloc;
+        out.has_user = true;
+    }
+    return DOT_OK;
+}
+
+int new_tree(const dot::DevAlloc &al, cudaStream_t s, dot_tree **out) {
+    dot_tree *t = new dot_tree();
+    if (cudaGetDevice(&t->device) != cudaSuccess) {
+        delete t;
+        return cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    }
+    t->alloc = al;
+    t->status = (uint32_t *)al.alloc(16, s);
+    if (!t->status) {
+        delete t;
+        return fail(DOT_ERR_OOM, "could not allocate the tree status word");
+    }
+    cudaError_t e = cudaMemsetAsync(t->status, 0, 16, s);
+    if (e != cudaSuccess) {
+        al.release(t->status, s);
+        delete t;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    *out = t;
+    return DOT_OK;
+}
+
+void destroy_tree(dot_tree *t) {
+    cudaDeviceSynchronize();
+    dot::free_tree_arrays(t->a, t->alloc, 0);
+    t->alloc.release(t->status, 0);
+    cudaStreamSynchronize(0);
+    delete t;
+}
+
+dot::TreeView view_of(const dot_tree *t) {
+    dot::TreeView tv;
+    tv.child = t->a.child;
+    tv.sigma = t->a.sigma;
+    tv.sh = t->a.sh;
+    tv.n_nodes = t->a.n_nodes;
+    tv.n_leaves = t->a.n_leaves;
+    tv.row_stride = t->a.row_stride;
+    tv.max_level = t->a.max_level;
+    for (int a = 0; a < 3; a++) tv.lo[a] = t->center[a] - t->half_size;
+    tv.size = 2.f * t->half_size;
+    tv.scale = 1.f / tv.size;
+    return tv;
+}
+
+int make_rays(const dot_rays *rays, dot::RaySource &rs, int64_t &n_rays) {
+    if (!rays) return fail(DOT_ERR_INVALID_ARG, "rays is NULL");
+    std::memset(&rs, 0, sizeof(rs));
+    rs.kind = rays->kind;
+    if (rays->kind == DOT_RAYS_BUFFER) {
+        if (rays->n_rays < 0) return fail(DOT_ERR_INVALID_ARG, "n_rays < 0");
+        if (rays->n_rays > 0 && (!rays->origins || !rays->dirs))
+            return fail(DOT_ERR_INVALID_ARG, "ray buffers are NULL");
+        if (rays->n_rays > ((int64_t)1 << 40)) return fail(DOT_ERR_INVALID_ARG, "too many rays");
+        rs.origins = rays->origins;
+        rs.dirs = rays->dirs;
+        rs.n_rays = rays->n_rays;
+        n_rays = rays->n_rays;
+        return DOT_OK;
+    }
+    if (rays->kind == DOT_RAYS_CAMERAS) {
+        if (rays->n_cameras < 0 || rays->n_cameras > 65535)
+            return fail(DOT_ERR_INVALID_ARG, "n_cameras must be in [0, 65535]");
+        if (rays->n_cameras > 0 && !rays->cameras) return fail(DOT_ERR_INVALID_ARG, "cameras is NULL");
+        if (rays->width <= 0 || rays->height <= 0 || rays->width > 65536 || rays->height > 65536)
+            return fail(DOT_ERR_INVALID_ARG, "camera width / height out of range");
+        rs.cams = rays->cameras;
+        rs.n_cams = rays->n_cameras;
+        rs.width = rays->width;
+        rs.height = rays->height;
+        rs.tiles_x = (rays->width + 15) / 16;
+        n_rays = (int64_t)rays->n_cameras * rays->width * rays->height;
+        rs.n_rays = n_rays;
+        return DOT_OK;
+    }
+    return fail(DOT_ERR_INVALID_ARG, "unknown rays kind");
+}
+
+int make_params(const dot_tree *t, const dot_render_opts *o, dot::RenderParams &rp, bool &exact) {
+    if (!o) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    if (!(o->eps_T >= 0.f && o->eps_T < 1.f)) return fail(DOT_ERR_INVALID_ARG, "eps_T must be in [0, 1)");
+    if (o->color_act != DOT_ACT_SIGMOID && o->color_act != DOT_ACT_LINEAR)
+        return fail(DOT_ERR_INVALID_ARG, "unknown color_act");
+    if (o->signal_mode < DOT_SIGNAL_NONE || o->signal_mode > DOT_SIGNAL_MAX_WEIGHT)
+        return fail(DOT_ERR_INVALID_ARG, "signal_mode of a render call must be NONE, SUM_ALPHA or MAX_WEIGHT");
+    if (o->precision < DOT_PRECISION_AUTO || o->precision > DOT_PRECISION_EXACT)
+        return fail(DOT_ERR_INVALID_ARG, "unknown precision");
+    if (o->max_steps < 0) return fail(DOT_ERR_INVALID_ARG, "max_steps < 0");
+    for (int c = 0; c < 3; c++) {
+        if (!std::isfinite(o->background[c])) return fail(DOT_ERR_INVALID_ARG, "background not finite");
+        rp.bg[c] = o->background[c];
+    }
+    rp.eps_T = o->eps_T;
+    rp.color_act = o->color_act;
+    rp.signal_mode = o->signal_mode;
+    rp.max_steps = o->max_steps ? o->max_steps : 3 * (1 << t->a.max_level) + 64;
+    exact = o->precision == DOT_PRECISION_EXACT ||
+            (o->precision == DOT_PRECISION_AUTO && t->a.storage == DOT_STORAGE_F32);
+    return DOT_OK;
+}
+
+int key_level_host(uint64_t key) {
+    int b = -1;
+    while (key) {
+        key >>= 1;
+        b++;
+    }
+    return b / 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dot_last_error(void) { return g_err.c_str(); }
+
+int dot_version(void) { return 100; }
+
+int dot_octree_build(const dot_build_desc *desc, const dot_allocator *alloc, void *stream,
+                     dot_tree **out) {
+    if (!desc || !out) return fail(DOT_ERR_INVALID_ARG, "desc and out must not be NULL");
+    if (desc->max_depth < 1 || desc->max_depth > dot::kMaxLevels)
+        return fail(DOT_ERR_INVALID_ARG, "max_depth must be in [1, 16]");
+    if (desc->sh_degree < 0 || desc->sh_degree > 3)
+        return fail(DOT_ERR_UNSUPPORTED, "sh_degree must be in [0, 3]");
+    if (desc->storage < DOT_STORAGE_F32 || desc->storage > DOT_STORAGE_BF16)
+        return fail(DOT_ERR_INVALID_ARG, "unknown storage type");
+    if (desc->n_primitives < 0 || desc->n_primitives > dot::kMaxPrimitives)
+        return fail(DOT_ERR_INVALID_ARG, "n_primitives must be in [0, 4096]");
+    if (desc->n_primitives > 0 && !desc->primitives)
+        return fail(DOT_ERR_INVALID_ARG, "primitives is NULL");
+    if (!(desc->half_size > 0.f) || !std::isfinite(desc->half_size))
+        return fail(DOT_ERR_INVALID_ARG, "half_size must be positive and finite");
+    for (int a = 0; a < 3; a++)
+        if (!std::isfinite(desc->center[a])) return fail(DOT_ERR_INVALID_ARG, "center not finite");
+    if (!std::isfinite(desc->density_lo) || !std::isfinite(desc->density_hi) ||
+        !std::isfinite(desc->sh_std) || !std::isfinite(desc->sh_dc))
+        return fail(DOT_ERR_INVALID_ARG, "parameter distribution not finite");
+    for (int i = 0; i < desc->n_primitives; i++) {
+        const dot_primitive &p = desc->primitives[i];
+        if (p.type < DOT_PRIM_SPHERE || p.type > DOT_PRIM_CYLINDER)
+            return fail(DOT_ERR_INVALID_ARG, "unknown primitive type");
+        for (int k = 0; k < 7; k++)
+            if (p.p[k] < -((int64_t)1 << 30) || p.p[k] > ((int64_t)1 << 30))
+                return fail(DOT_ERR_INVALID_ARG, "primitive parameter out of range (|p| <= 2^30)");
+    }
+    dot::DevAlloc al;
+    int rc = make_alloc(alloc, al);
+    if (rc) return rc;
+    dot_tree *t = nullptr;
+    rc = new_tree(al, S(stream), &t);
+    if (rc) return rc;
+    for (int a = 0; a < 3; a++) t->center[a] = desc->center[a];
+    t->half_size = desc->half_size;
+    cudaError_t e = dot::build_tree(*desc, t->a, al, S(stream));
+    if (e != cudaSuccess) {
+        int r = cuda_fail(e, "dot_octree_build");
+        destroy_tree(t);
+        return r;
+    }
+    *out = t;
+    return DOT_OK;
+}
+
+int dot_tree_free(dot_tree *tree) {
+    if (!tree) return DOT_OK;
+    destroy_tree(tree);
+    return DOT_OK;
+}
+
+int dot_tree_get_info(const dot_tree *t, dot_tree_info *info) {
+    if (!t || !info) return fail(DOT_ERR_INVALID_ARG, "tree and info must not be NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->n_nodes = t->a.n_nodes;
+    info->n_leaves = t->a.n_leaves;
+    info->max_level = t->a.max_level;
+    info->sh_degree = t->a.sh_degree;
+    info->n_coeffs = t->a.K;
+    info->storage = t->a.storage;
+    info->sh_row_stride = t->a.row_stride;
+    for (int a = 0; a < 3; a++) info->center[a] = t->center[a];
+    info->half_size = t->half_size;
+    info->child = t->a.child;
+    info->node_parent = t->a.node_parent;
+    info->node_key = t->a.node_key;
+    info->leaf_parent = t->a.leaf_parent;
+    info->leaf_key = t->a.leaf_key;
+    info->sigma = t->a.sigma;
+    info->sh = t->a.sh;
+    return DOT_OK;
+}
+
+int dot_tree_export(const dot_tree *t, void *stream, int32_t *child, int32_t *node_parent,
+                    uint64_t *node_key, int32_t *leaf_parent, uint64_t *leaf_key, void *sigma,
+                    void *sh) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const auto &a = t->a;
+    const size_t sb = (size_t)dot::storage_bytes(a.storage);
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        if (!dst || bytes == 0) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    API_CK(cp(child, a.child, (size_t)a.n_nodes * 8 * 4), "export child");
+    API_CK(cp(node_parent, a.node_parent, (size_t)a.n_nodes * 4), "export node_parent");
+    API_CK(cp(node_key, a.node_key, (size_t)a.n_nodes * 8), "export node_key");
+    API_CK(cp(leaf_parent, a.leaf_parent, (size_t)a.n_leaves * 4), "export leaf_parent");
+    API_CK(cp(leaf_key, a.leaf_key, (size_t)a.n_leaves * 8), "export leaf_key");
+    API_CK(cp(sigma, a.sigma, (size_t)a.n_leaves * sb), "export sigma");
+    if (sh && a.n_leaves > 0)
+        API_CK(cudaMemcpy2DAsync(sh, 3 * a.K * sb, a.sh, (size_t)a.row_stride * sb, 3 * a.K * sb,
+                                 (size_t)a.n_leaves, cudaMemcpyDeviceToHost, s),
+               "export sh");
+    API_CK(cudaStreamSynchronize(s), "export sync");
+    return DOT_OK;
+}
+
+int dot_tree_import(const dot_host_tree *h, const dot_allocator *alloc, void *stream,
+                    dot_tree **out) {
+    if (!h || !out) return fail(DOT_ERR_INVALID_ARG, "host tree and out must not be NULL");
+    const int64_t N = h->n_nodes, L = h->n_leaves;
+    if (N < 1 || L < 1 || N > (int64_t)INT32_MAX / 8 || L > (int64_t)INT32_MAX)
+        return fail(DOT_ERR_INVALID_ARG, "node / leaf counts out of range");
+    if (h->sh_degree < 0 || h->sh_degree > 3) return fail(DOT_ERR_UNSUPPORTED, "sh_degree must be in [0, 3]");
+    if (h->storage < DOT_STORAGE_F32 || h->storage > DOT_STORAGE_BF16)
+        return fail(DOT_ERR_INVALID_ARG, "unknown storage type");
+    if (!h->child || !h->node_parent || !h->node_key || !h->leaf_parent || !h->leaf_key ||
+        !h->sigma || !h->sh)
+        return fail(DOT_ERR_INVALID_ARG, "host arrays must not be NULL");
+    if (!(h->half_size > 0.f)) return fail(DOT_ERR_INVALID_ARG, "half_size must be positive");
+    // structural validation: every node but the root and every leaf referenced once, parents
+    // and keys consistent, levels <= 16
+    std::vector<uint8_t> seen_n((size_t)N, 0), seen_l((size_t)L, 0);
+    if (h->node_key[0] != 1 || h->node_parent[0] != -1)
+        return fail(DOT_ERR_INVALID_ARG, "node 0 must be the root (key 1, parent -1)");
+    int max_level = 0;
+    for (int64_t p = 0; p < N; p++) {
+        if (key_level_host(h->node_key[p]) >= dot::kMaxLevels)
+            return fail(DOT_ERR_INVALID_ARG, "internal node below level 15");
+        for (int j = 0; j < 8; j++) {
+            const int32_t c = h->child[8 * p + j];
+            const uint64_t ck = (h->node_key[p] << 3) | (uint64_t)j;
+            if (c >= 0) {
+                if (c == 0 || c >= N || seen_n[c]) return fail(DOT_ERR_INVALID_ARG, "bad internal child pointer");
+                seen_n[c] = 1;
+                if (h->node_parent[c] != p || h->node_key[c] != ck)
+                    return fail(DOT_ERR_INVALID_ARG, "node parent / key inconsistent with child table");
+            } else {
+                const int64_t v = -1 - (int64_t)c;
+                if (v >= L || seen_l[v]) return fail(DOT_ERR_INVALID_ARG, "bad leaf child pointer");
+                seen_l[v] = 1;
+                if (h->leaf_parent[v] != p || h->leaf_key[v] != ck)
+                    return fail(DOT_ERR_INVALID_ARG, "leaf parent / key inconsistent with child table");
+                const int lv = key_level_host(ck);
+                if (lv > max_level) max_level = lv;
+            }
+        }
+    }
+    for (int64_t p = 1; p < N; p++)
+        if (!seen_n[p]) return fail(DOT_ERR_INVALID_ARG, "unreferenced internal node");
+    for (int64_t v = 0; v < L; v++)
+        if (!seen_l[v]) return fail(DOT_ERR_INVALID_ARG, "unreferenced leaf");
+    dot::DevAlloc al;
+    int rc = make_alloc(alloc, al);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    dot_tree *t = nullptr;
+    rc = new_tree(al, s, &t);
+    if (rc) return rc;
+    for (int a = 0; a < 3; a++) t->center[a] = h->center[a];
+    t->half_size = h->half_size;
+    t->a.n_nodes = N;
+    t->a.n_leaves = L;
+    t->a.max_level = max_level;
+    t->a.sh_degree = h->sh_degree;
+    t->a.storage = h->storage;
+    t->a.K = (h->sh_degree + 1) * (h->sh_degree + 1);
+    t->a.row_stride = dot::row_stride_elems(h->storage, t->a.K);
+    cudaError_t e = dot::alloc_tree_arrays(t->a, al, s);
+    const size_t sb = (size_t)dot::storage_bytes(h->storage);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.child, h->child, (size_t)N * 32, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.node_parent, h->node_parent, (size_t)N * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.node_key, h->node_key, (size_t)N * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.leaf_parent, h->leaf_parent, (size_t)L * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.leaf_key, h->leaf_key, (size_t)L * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t->a.sigma, h->sigma, (size_t)L * sb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->a.sh, 0, (size_t)L * t->a.row_stride * sb, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(t->a.sh, (size_t)t->a.row_stride * sb, h->sh, 3 * t->a.K * sb,
+                              3 * t->a.K * sb, (size_t)L, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(e, "dot_tree_import");
+        destroy_tree(t);
+        return r;
+    }
+    *out = t;
+    return DOT_OK;
+}
+
+int dot_tree_status(dot_tree *t, void *stream, uint32_t *status) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!status) return fail(DOT_ERR_INVALID_ARG, "status is NULL");
+    uint32_t h = 0;
+    API_CK(cudaMemcpyAsync(&h, t->status, 4, cudaMemcpyDeviceToHost, S(stream)), "status read");
+    API_CK(cudaMemsetAsync(t->status, 0, 4, S(stream)), "status clear");
+    API_CK(cudaStreamSynchronize(S(stream)), "status sync");
+    *status = h;
+    return DOT_OK;
+}
+
+int dot_render_forward(const dot_tree *t, const dot_rays *rays, const dot_render_opts *opts,
+                       float *rgb, float *T_final, float *signal, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    dot::RaySource rs;
+    int64_t R = 0;
+    if ((rc = make_rays(rays, rs, R))) return rc;
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    if (R > 0 && !rgb) return fail(DOT_ERR_INVALID_ARG, "rgb is NULL");
+    if (rp.signal_mode != DOT_SIGNAL_NONE && !signal)
+        return fail(DOT_ERR_INVALID_ARG, "signal_mode set but signal is NULL");
+    dot::RenderIO io{};
+    io.rgb = rgb;
+    io.T_final = T_final;
+    io.signal = rp.signal_mode != DOT_SIGNAL_NONE ? signal : nullptr;
+    io.status = t->status;
+    if (R == 0) return DOT_OK;
+    API_CK(dot::launch_march_fwd(t->a.storage, t->a.sh_degree, exact, view_of(t), rs, rp, io, S(stream)),
+           "dot_render_forward");
+    return DOT_OK;
+}
+
+int dot_render_backward(const dot_tree *t, const dot_rays *rays, const dot_render_opts *opts,
+                        const float *grad_rgb, const float *rgb, float *grad_sigma,
+                        float *grad_sh, float *signal, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    dot::RaySource rs;
+    int64_t R = 0;
+    if ((rc = make_rays(rays, rs, R))) return rc;
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    if (R > 0 && (!grad_rgb || !rgb || !grad_sigma || !grad_sh))
+        return fail(DOT_ERR_INVALID_ARG, "grad_rgb, rgb, grad_sigma and grad_sh must not be NULL");
+    if (rp.signal_mode != DOT_SIGNAL_NONE && !signal)
+        return fail(DOT_ERR_INVALID_ARG, "signal_mode set but signal is NULL");
+    dot::RenderIO io{};
+    io.grad_rgb = grad_rgb;
+    io.rgb_fwd = rgb;
+    io.grad_sigma = grad_sigma;
+    io.grad_sh = grad_sh;
+    io.signal = rp.signal_mode != DOT_SIGNAL_NONE ? signal : nullptr;
+    io.status = t->status;
+    io.grad_vec = ((reinterpret_cast<uintptr_t>(grad_sh) & 15u) == 0) ? 1 : 0;
+    if (R == 0) return DOT_OK;
+    API_CK(dot::launch_march_bwd(t->a.storage, t->a.sh_degree, exact, view_of(t), rs, rp, io, S(stream)),
+           "dot_render_backward");
+    return DOT_OK;
+}
+
+int dot_accumulate_signal(const dot_tree *t, const dot_rays *rays, const dot_render_opts *opts,
+                          int32_t mode, float *signal, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!signal) return fail(DOT_ERR_INVALID_ARG, "signal is NULL");
+    if (mode == DOT_SIGNAL_SIGMA) {
+        API_CK(dot::launch_sigma_signal(t->a.storage, t->a.sigma, t->a.n_leaves, signal, S(stream)),
+               "dot_accumulate_signal");
+        return DOT_OK;
+    }
+    if (mode != DOT_SIGNAL_SUM_ALPHA && mode != DOT_SIGNAL_MAX_WEIGHT)
+        return fail(DOT_ERR_INVALID_ARG, "mode must be SUM_ALPHA, MAX_WEIGHT or SIGMA");
+    dot::RaySource rs;
+    int64_t R = 0;
+    if ((rc = make_rays(rays, rs, R))) return rc;
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    rp.signal_mode = mode;
+    dot::RenderIO io{};
+    io.signal = signal;
+    io.status = t->status;
+    if (R == 0) return DOT_OK;
+    API_CK(dot::launch_march_signal(t->a.storage, exact, view_of(t), rs, rp, io, S(stream)),
+           "dot_accumulate_signal");
+    return DOT_OK;
+}
+
+int dot_select_masks(const dot_tree *t, const float *signal, const dot_select_opts *opts,
+                     uint8_t *prune_mark, uint8_t *sample_mark, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    const int64_t L = t->a.n_leaves;
+    for (int m : {opts->prune_mode, opts->sample_mode})
+        if (m < DOT_SELECT_NONE || m > DOT_SELECT_FRACTION)
+            return fail(DOT_ERR_INVALID_ARG, "unknown selection mode");
+    if ((opts->prune_mode == DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
+        (opts->sample_mode == DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
+        return fail(DOT_ERR_INVALID_ARG, "selection fraction must be in [0, 1]");
+    if (L > 0 && (!signal || !prune_mark || !sample_mark))
+        return fail(DOT_ERR_INVALID_ARG, "signal and masks must not be NULL");
+    API_CK(dot::select_masks(signal, L, opts->prune_mode, opts->prune_value, opts->sample_mode,
+                             opts->sample_value, prune_mark, sample_mark, S(stream)),
+           "dot_select_masks");
+    return DOT_OK;
+}
+
+int dot_refine_plan(const dot_tree *t, const uint8_t *prune_mark, const uint8_t *sample_mark,
+                    int32_t depth_cap, dot_refine_counts *out, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!prune_mark || !sample_mark || !out) return fail(DOT_ERR_INVALID_ARG, "masks and out must not be NULL");
+    if (depth_cap < 1 || depth_cap > dot::kMaxLevels) return fail(DOT_ERR_INVALID_ARG, "depth_cap must be in [1, 16]");
+    dot::RefinePlan plan{};
+    API_CK(dot::refine_tree(t->a, prune_mark, sample_mark, depth_cap, false, nullptr, t->alloc,
+                            nullptr, nullptr, 0, &plan, S(stream)),
+           "dot_refine_plan");
+    out->n_nodes = plan.n_nodes;
+    out->n_leaves = plan.n_leaves;
+    out->n_pruned_groups = plan.n_merged;
+    out->n_sampled = plan.n_sampled;
+    out->n_capped = plan.n_capped;
+    return DOT_OK;
+}
+
+int dot_refine_prune(dot_tree *t, const uint8_t *prune_mark, const uint8_t *sample_mark,
+                     int32_t depth_cap, int32_t *leaf_map, const dot_leaf_array *aux, int32_t n_aux,
+                     void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!prune_mark || !sample_mark || !leaf_map) return fail(DOT_ERR_INVALID_ARG, "masks and leaf_map must not be NULL");
+    if (depth_cap < 1 || depth_cap > dot::kMaxLevels) return fail(DOT_ERR_INVALID_ARG, "depth_cap must be in [1, 16]");
+    if (n_aux < 0 || (n_aux > 0 && !aux)) return fail(DOT_ERR_INVALID_ARG, "bad aux arrays");
+    for (int i = 0; i < n_aux; i++) {
+        if (!aux[i].src || !aux[i].dst || aux[i].width < 1)
+            return fail(DOT_ERR_INVALID_ARG, "aux array needs src, dst and width >= 1");
+        if (aux[i].merge < DOT_MERGE_MEAN || aux[i].merge > DOT_MERGE_MAX)
+            return fail(DOT_ERR_INVALID_ARG, "unknown aux merge");
+    }
+    dot::RefinePlan plan{};
+    dot::TreeArrays nw;
+    API_CK(dot::refine_tree(t->a, prune_mark, sample_mark, depth_cap, true, &nw, t->alloc, leaf_map,
+                            aux, n_aux, &plan, S(stream)),
+           "dot_refine_prune");
+    dot::free_tree_arrays(t->a, t->alloc, S(stream));
+    t->a = nw;
+    return DOT_OK;
+}
+
+int dot_render_stats(const dot_tree *t, const dot_rays *rays, const dot_render_opts *opts,
+                     int64_t out[4], void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!out) return fail(DOT_ERR_INVALID_ARG, "out is NULL");
+    dot::RaySource rs;
+    int64_t R = 0;
+    if ((rc = make_rays(rays, rs, R))) return rc;
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    cudaStream_t s = S(stream);
+    unsigned long long *d = nullptr;
+    API_CK(cudaMallocAsync((void **)&d, 4 * sizeof(unsigned long long), s), "stats alloc");
+    dot::RenderIO io{};
+    io.stats = d;
+    io.status = t->status;
+    cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess && R > 0) e = dot::launch_march_stats(t->a.storage, exact, view_of(t), rs, rp, io, s);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dot_render_stats");
+    for (int i = 0; i < 4; i++) out[i] = (int64_t)h[i];
+    return DOT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,449 @@
+// march.cuh -- one ray's march through the octree, shared by the forward, backward, signal and
+// statistics kernels so that every mode sees bit-identical segments and transmittance.
+//
+// Per ray (Sec. 3 Preliminaries; Eq. 1-2):
+//   1. slab test against the root cube, entry t0 >= 0;
+//   2. the current cell is kept as integer coordinates g on the 2^16 grid; the leaf holding g is
+//      found by descending child pointers, restarting from the deepest common ancestor of the
+//      previous leaf (kept in a per-thread path stack in shared memory);
+//   3. the leaf's exit time is the nearest of its three exit faces; delta = t_exit - t;
+//   4. occupied segments (sigma > 0) are shaded: SH colour, alpha = 1 - exp(-sigma delta),
+//      w = T alpha, C += w c, T *= exp(-sigma delta); the march stops once T < eps_T;
+//   5. the next cell steps across every exit face hit at t_exit (edges and corners included) and
+//      keeps the other coordinates of the exit point clamped into the old cell.
+// Plane times are computed from the plane's exact coordinate, never accumulated, so neighbouring
+// cells agree bit for bit on shared faces and segment lengths telescope.  In exact mode they are
+// float-float values (about 44 bits), in fast mode float32.
+#pragma once
+
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace dot {
+
+// ---------------------------------------------------------------------------------------------
+// real spherical-harmonic constants from their closed forms, evaluated at compile time
+// ---------------------------------------------------------------------------------------------
+namespace cexpr {
+constexpr double newton_sqrt(double x, double g, int n) {
+    return n == 0 ? g : newton_sqrt(x, 0.5 * (g + x / g), n - 1);
+}
+constexpr double sqrt(double x) { return newton_sqrt(x, x < 1.0 ? 1.0 : x, 80); }
+constexpr double pi = 3.14159265358979323846264338327950288;
+}  // namespace cexpr
+
+constexpr float kY00 = float(1.0 / (2.0 * cexpr::sqrt(cexpr::pi)));          // 1 / (2 sqrt(pi))
+constexpr float kY1 = float(cexpr::sqrt(3.0 / (4.0 * cexpr::pi)));            // sqrt(3 / 4pi)
+constexpr float kY2a = float(cexpr::sqrt(15.0 / cexpr::pi) / 2.0);            // sqrt(15/pi) / 2
+constexpr float kY2b = float(cexpr::sqrt(5.0 / cexpr::pi) / 4.0);             // sqrt(5/pi) / 4
+constexpr float kY2c = float(cexpr::sqrt(15.0 / cexpr::pi) / 4.0);            // sqrt(15/pi) / 4
+constexpr float kY3p = float(cexpr::sqrt(35.0 / (2.0 * cexpr::pi)) / 4.0);    // sqrt(35/2pi) / 4
+constexpr float kY3q = float(cexpr::sqrt(105.0 / cexpr::pi) / 2.0);           // sqrt(105/pi) / 2
+constexpr float kY3s = float(cexpr::sqrt(21.0 / (2.0 * cexpr::pi)) / 4.0);    // sqrt(21/2pi) / 4
+constexpr float kY3u = float(cexpr::sqrt(7.0 / cexpr::pi) / 4.0);             // sqrt(7/pi) / 4
+constexpr float kY3v = float(cexpr::sqrt(105.0 / cexpr::pi) / 4.0);           // sqrt(105/pi) / 4
+
+// real SH basis Y_k (k = l^2 + l + m) at the unit direction (x, y, z), degrees 0..deg(K)
+template <int K>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+    Y[0] = kY00;
+    if constexpr (K > 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+    }
+    if constexpr (K > 4) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * (x * y);
+        Y[5] = -kY2a * (y * z);
+        Y[6] = kY2b * (2.f * zz - xx - yy);
+        Y[7] = -kY2a * (x * z);
+        Y[8] = kY2c * (xx - yy);
+        if constexpr (K > 9) {
+            Y[9] = -kY3p * y * (3.f * xx - yy);
+            Y[10] = kY3q * (x * y) * z;
+            Y[11] = -kY3s * y * (4.f * zz - xx - yy);
+            Y[12] = kY3u * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3s * x * (4.f * zz - xx - yy);
+            Y[14] = kY3v * z * (xx - yy);
+            Y[15] = -kY3p * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// SH rows: [3][K] coefficients in the storage type, padded to 16-byte vectors
+// ---------------------------------------------------------------------------------------------
+template <typename S, int K> struct Row {
+    static constexpr int kBytes = ((3 * K * (int)sizeof(S) + 15) / 16) * 16;
+    static constexpr int kVec = kBytes / 16;
+};
+
+template <typename S, int K>
+__device__ __forceinline__ void leaf_z(const S *row, const float *Y, float z[3]) {
+    uint4 v[Row<S, K>::kVec];
+    const uint4 *p = reinterpret_cast<const uint4 *>(row);
+#pragma unroll
+    for (int i = 0; i < Row<S, K>::kVec; i++) v[i] = __ldg(p + i);
+    const S *e = reinterpret_cast<const S *>(v);
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) acc = fmaf(Storage<S>::to_f32(e[ch * K + k]), Y[k], acc);
+        z[ch] = acc;
+    }
+}
+
+template <bool EXACT> __device__ __forceinline__ float ex(float x) {
+    if constexpr (EXACT) return expf(x);
+    else return __expf(x);
+}
+
+template <bool EXACT> __device__ __forceinline__ float sigmoid(float z) {
+    if constexpr (EXACT) return 1.f / (1.f + expf(-z));
+    else return __fdividef(1.f, 1.f + __expf(-z));
+}
+
+// ---------------------------------------------------------------------------------------------
+// plane times
+// ---------------------------------------------------------------------------------------------
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool lt(FF a, FF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool eq(float a, float b) { return a == b; }
+__device__ __forceinline__ bool eq(FF a, FF b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ float val(float a) { return a; }
+__device__ __forceinline__ float val(FF a) { return a.hi + a.lo; }
+__device__ __forceinline__ float diff(float a, float b) { return a - b; }
+// a - b for close a, b: the high parts subtract exactly (Sterbenz), the low parts add the rest
+__device__ __forceinline__ float diff(FF a, FF b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+template <typename P> __device__ __forceinline__ P pinf();
+template <> __device__ __forceinline__ float pinf<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ FF pinf<FF>() { return FF{__int_as_float(0x7f800000), 0.f}; }
+template <typename P> __device__ __forceinline__ P pzero();
+template <> __device__ __forceinline__ float pzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ FF pzero<FF>() { return FF{0.f, 0.f}; }
+
+// Ray state for plane-time evaluation.  Fast: t(x) = x * inv + c on normalised coordinates.
+// Exact: t(x) = (lo + x size - o) / d in world units, as a float-float (error-free product and
+// sums, one Newton-corrected quotient).
+struct RayAxes {
+    float on[3], dn[3];      // normalised origin and direction (root = [0,1]^3)
+    int sg[3];               // direction signs
+    float inv[3], c[3];      // fast mode
+    float ow[3], dw[3], invw[3], lo[3], size;  // exact mode
+};
+
+template <bool EXACT>
+__device__ __forceinline__ typename std::conditional<EXACT, FF, float>::type
+plane_t(const RayAxes &r, int a, float x) {
+    if constexpr (!EXACT) {
+        return fmaf(x, r.inv[a], r.c[a]);
+    } else {
+        const float p = x * r.size;
+        const float pe = fmaf(x, r.size, -p);            // x size = p + pe exactly
+        float s = r.lo[a] + p;                            // two-sum(lo, p)
+        float bb = s - r.lo[a];
+        float e = (r.lo[a] - (s - bb)) + (p - bb);
+        e += pe;
+        const float m = -r.ow[a];
+        float n = s + m;                                   // two-sum(s, -o)
+        float b2 = n - s;
+        float ne = (s - (n - b2)) + (m - b2);
+        ne += e;
+        const float q = n * r.invw[a];
+        const float rem = fmaf(-q, r.dw[a], n) + ne;      // remainder of the quotient
+        const float q2 = rem * r.invw[a];
+        const float hi = q + q2;
+        return FF{hi, q2 - (hi - q)};
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// the march
+// ---------------------------------------------------------------------------------------------
+struct RayOut {
+    float rgb[3];
+    float T;
+    unsigned long long st[4];  // STATS: hit, steps, occupied, child loads
+};
+
+template <typename S, int K, int MODE, bool EXACT>
+__device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams &rp,
+                                          const RenderIO &io, int64_t ray, const float ow[3],
+                                          const float dw[3], int32_t *stack, RayOut &out) {
+    using PT = typename std::conditional<EXACT, FF, float>::type;
+    RayAxes r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        r.on[a] = (ow[a] - tv.lo[a]) * tv.scale;
+        r.dn[a] = dw[a] * tv.scale;
+        r.sg[a] = r.dn[a] > 0.f ? 1 : (r.dn[a] < 0.f ? -1 : 0);
+        if constexpr (!EXACT) {
+            r.inv[a] = 1.f / r.dn[a];
+            r.c[a] = -r.on[a] * r.inv[a];
+        } else {
+            r.ow[a] = ow[a];
+            r.dw[a] = dw[a];
+            r.invw[a] = 1.f / dw[a];
+            r.lo[a] = tv.lo[a];
+        }
+    }
+    if constexpr (EXACT) r.size = tv.size;
+
+    float T = 1.f;
+    float C[3] = {0.f, 0.f, 0.f};
+    out.T = 1.f;
+
+    // ---- root slab ----
+    PT tn = pzero<PT>(), tf = pinf<PT>();
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (r.sg[a] == 0) {
+            if (!(r.on[a] >= 0.f && r.on[a] <= 1.f)) hit = false;
+        } else {
+            const PT t0 = plane_t<EXACT>(r, a, r.sg[a] > 0 ? 0.f : 1.f);
+            const PT t1 = plane_t<EXACT>(r, a, r.sg[a] > 0 ? 1.f : 0.f);
+            if (lt(tn, t0)) tn = t0;
+            if (lt(t1, tf)) tf = t1;
+        }
+    }
+    if (!hit || !lt(tn, tf)) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) out.rgb[ch] = rp.bg[ch];
+        return;
+    }
+    if constexpr (MODE == kStats) out.st[0] += 1;
+
+    float Y[K];
+    if constexpr (MODE == kFwd || MODE == kBwd) sh_basis<K>(dw[0], dw[1], dw[2], Y);
+    float g[3], rgbf[3];
+    if constexpr (MODE == kBwd) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            g[ch] = __ldg(io.grad_rgb + 3 * ray + ch);
+            rgbf[ch] = __ldg(io.rgb_fwd + 3 * ray + ch);
+        }
+    }
+
+    // ---- first cell ----
+    int gc[3];
+    {
+        const float t0 = val(tn);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float p = fmaf(t0, r.dn[a], r.on[a]);
+            const int gi = (int)floorf(p * 65536.f);
+            gc[a] = min(max(gi, 0), 65535);
+        }
+    }
+
+    const S *sigma = reinterpret_cast<const S *>(tv.sigma);
+    const S *shp = reinterpret_cast<const S *>(tv.sh);
+    PT t = tn;
+    int32_t node = 0;
+    int level = 0;
+    int steps = 0;
+    while (true) {
+        if (steps >= rp.max_steps) {
+            atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
+            break;
+        }
+        ++steps;
+        // descend from (node, level) to the leaf holding gc
+        int32_t c;
+        while (true) {
+            const int sh = kGridBits - 1 - level;
+            const int j = (((gc[0] >> sh) & 1) << 2) | (((gc[1] >> sh) & 1) << 1) | ((gc[2] >> sh) & 1);
+            stack[level * kMarchThreads] = node;
+            c = __ldg(tv.child + (int64_t)node * 8 + j);
+            ++level;
+            if constexpr (MODE == kStats) out.st[3] += 1;
+            if (c < 0 || level >= tv.max_level) break;
+            node = c;
+        }
+        if (c >= 0) {  // deeper than the tree claims: corrupted table, stop the ray
+            atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
+            break;
+        }
+        const int32_t leaf = -1 - c;
+        const int cs = 1 << (kGridBits - level);
+        int lo_g[3];
+        PT te[3];
+        PT tout = pinf<PT>();
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo_g[a] = gc[a] & ~(cs - 1);
+            if (r.sg[a] != 0) {
+                const int f = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a];
+                te[a] = plane_t<EXACT>(r, a, (float)f * (1.f / 65536.f));
+                if (lt(te[a], tout)) tout = te[a];
+            } else {
+                te[a] = pinf<PT>();
+            }
+        }
+        if (!(val(tout) < pinf<float>())) break;  // only for a zero direction
+        const float delta = diff(tout, t);
+
+        if constexpr (MODE == kStats) out.st[1] += 1;
+        bool stop = false;
+        if (delta > 0.f) {
+            const float sv = Storage<S>::load(sigma + leaf);
+            if (sv > 0.f) {
+                if constexpr (MODE == kStats) out.st[2] += 1;
+                const float e = ex<EXACT>(-(sv * delta));
+                const float alpha = 1.f - e;
+                const float w = T * alpha;
+                if constexpr (MODE == kFwd || MODE == kBwd) {
+                    float z[3], col[3];
+                    leaf_z<S, K>(shp + (int64_t)leaf * tv.row_stride, Y, z);
+#pragma unroll
+                    for (int ch = 0; ch < 3; ch++)
+                        col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
+#pragma unroll
+                    for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
+                    if constexpr (MODE == kBwd) {
+                        const float Tn = T * e;
+                        float acc = 0.f;
+                        float dz[3];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ch++) {
+                            const float suffix = rgbf[ch] - C[ch];
+                            acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
+                            const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
+                            dz[ch] = g[ch] * w * ag;
+                        }
+                        atomicAdd(io.grad_sigma + leaf, delta * acc);
+                        float *gr = io.grad_sh + (int64_t)leaf * (3 * K);
+                        if constexpr ((3 * K) % 4 == 0) {
+                            if (io.grad_vec) {
+                                float4 *g4 = reinterpret_cast<float4 *>(gr);
+#pragma unroll
+                                for (int q = 0; q < 3 * K / 4; q++) {
+                                    float4 v;
+                                    v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
+                                    v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
+                                    v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
+                                    v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
+                                    atomicAdd(g4 + q, v);
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                        }
+                    }
+                }
+                if (MODE != kStats && io.signal != nullptr) {
+                    if (rp.signal_mode == DOT_SIGNAL_SUM_ALPHA) atomicAdd(io.signal + leaf, alpha);
+                    else if (rp.signal_mode == DOT_SIGNAL_MAX_WEIGHT)
+                        atomicMax(reinterpret_cast<int *>(io.signal) + leaf, __float_as_int(w));
+                }
+                T = T * e;
+                stop = T < rp.eps_T;
+            }
+        }
+        if (stop) break;
+
+        // ---- next cell ----
+        bool outside = false;
+        const float toutv = val(tout);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (r.sg[a] != 0 && eq(te[a], tout)) {
+                gc[a] = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a] - 1;
+                outside |= (gc[a] < 0) | (gc[a] > 65535);
+            } else {
+                const float p = fmaf(toutv, r.dn[a], r.on[a]);
+                const int gi = (int)floorf(p * 65536.f);
+                gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
+            }
+        }
+        if (outside) break;
+        if (lt(t, tout)) t = tout;
+        const unsigned dbits = (unsigned)((gc[0] ^ lo_g[0]) | (gc[1] ^ lo_g[1]) | (gc[2] ^ lo_g[2]));
+        level = kGridBits - 1 - (31 - __clz(dbits));
+        node = stack[level * kMarchThreads];
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) out.rgb[ch] = fmaf(T, rp.bg[ch], C[ch]);
+    out.T = T;
+}
+
+// ray of a thread: pinhole pixel (bit-exact float32 recipe of dot_camera) or a buffer entry
+__device__ __forceinline__ void camera_ray(const dot_camera *cam, int i, int j, float o[3], float d[3]) {
+    const float fx = __ldg(&cam->fx), fy = __ldg(&cam->fy), cx = __ldg(&cam->cx), cy = __ldg(&cam->cy);
+    const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), cx), fx);
+    const float yc = -__fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), cy), fy);
+    float e[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float r0 = __ldg(&cam->c2w[4 * a + 0]), r1 = __ldg(&cam->c2w[4 * a + 1]);
+        const float r2 = __ldg(&cam->c2w[4 * a + 2]);
+        e[a] = __fsub_rn(__fadd_rn(__fmul_rn(r0, xc), __fmul_rn(r1, yc)), r2);
+        o[a] = __ldg(&cam->c2w[4 * a + 3]);
+    }
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(e[0], e[0]), __fmul_rn(e[1], e[1])), __fmul_rn(e[2], e[2]));
+    const float inv = __fdiv_rn(1.f, __fsqrt_rn(n2));
+#pragma unroll
+    for (int a = 0; a < 3; a++) d[a] = __fmul_rn(e[a], inv);
+}
+
+template <typename S, int K, int MODE, bool EXACT>
+__global__ void __launch_bounds__(kMarchThreads)
+march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
+    __shared__ int32_t s_stack[kMaxLevels * kMarchThreads];
+    int32_t *stack = s_stack + threadIdx.x;
+
+    int64_t ray;
+    bool valid;
+    float ow[3], dw[3];
+    if (rs.kind == DOT_RAYS_CAMERAS) {
+        const int tx = blockIdx.x % rs.tiles_x, ty = blockIdx.x / rs.tiles_x;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int px = tx * 16 + (warp & 1) * 8 + (lane & 7);
+        const int py = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+        valid = px < rs.width && py < rs.height;
+        ray = ((int64_t)blockIdx.y * rs.height + py) * rs.width + px;
+        if (valid) camera_ray(rs.cams + blockIdx.y, px, py, ow, dw);
+    } else {
+        ray = (int64_t)blockIdx.x * kMarchThreads + threadIdx.x;
+        valid = ray < rs.n_rays;
+        if (valid) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                ow[a] = __ldg(rs.origins + 3 * ray + a);
+                dw[a] = __ldg(rs.dirs + 3 * ray + a);
+            }
+        }
+    }
+    RayOut out;
+    out.st[0] = out.st[1] = out.st[2] = out.st[3] = 0;
+    if (valid) {
+        march_ray<S, K, MODE, EXACT>(tv, rp, io, ray, ow, dw, stack, out);
+        if constexpr (MODE == kFwd) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) io.rgb[3 * ray + ch] = out.rgb[ch];
+            if (io.T_final) io.T_final[ray] = out.T;
+        }
+    }
+    if constexpr (MODE == kStats) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            unsigned long long v = out.st[i];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(io.stats + i, v);
+        }
+    }
+}
+
+}  // namespace dot

@@ -1,0 +1,505 @@
+"""Thin ctypes binding of ``libdot.so`` (include/dot.h), with the same entry-point names.
+
+Only argument marshalling lives here: every step of the path runs in the CUDA library.  Device
+buffers are torch CUDA tensors (PyTorch supplies device memory and the current stream).  If the
+library cannot be loaded the import fails; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+# ----------------------------------------------------------------------------------------------
+# constants (mirror include/dot.h)
+# ----------------------------------------------------------------------------------------------
+DOT_OK = 0
+DOT_ERR_INVALID_ARG = -1
+DOT_ERR_OOM = -2
+DOT_ERR_CUDA = -3
+DOT_ERR_STEP_LIMIT = -4
+DOT_ERR_UNSUPPORTED = -5
+
+DOT_STORAGE_F32, DOT_STORAGE_F16, DOT_STORAGE_BF16 = 0, 1, 2
+DOT_ACT_SIGMOID, DOT_ACT_LINEAR = 0, 1
+DOT_SIGNAL_NONE, DOT_SIGNAL_SUM_ALPHA, DOT_SIGNAL_MAX_WEIGHT, DOT_SIGNAL_SIGMA = 0, 1, 2, 3
+DOT_SELECT_NONE, DOT_SELECT_THRESHOLD, DOT_SELECT_FRACTION = 0, 1, 2
+DOT_MERGE_MEAN, DOT_MERGE_SUM, DOT_MERGE_MAX = 0, 1, 2
+DOT_RAYS_BUFFER, DOT_RAYS_CAMERAS = 0, 1
+DOT_PRECISION_AUTO, DOT_PRECISION_FAST, DOT_PRECISION_EXACT = 0, 1, 2
+DOT_STATUS_STEP_LIMIT = 1
+
+ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_free",
+                "dot_tree_get_info", "dot_tree_export", "dot_tree_import", "dot_tree_status",
+                "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
+                "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats")
+
+_TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
+                     DOT_STORAGE_BF16: torch.bfloat16}
+_NP_OF_STORAGE = {DOT_STORAGE_F32: np.float32, DOT_STORAGE_F16: np.float16,
+                  DOT_STORAGE_BF16: np.uint16}
+
+P = ctypes.c_void_p
+
+
+class DotError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libdot error {code}: {msg}")
+        self.code = code
+
+
+# ----------------------------------------------------------------------------------------------
+# structures
+# ----------------------------------------------------------------------------------------------
+_ALLOC_FN = ctypes.CFUNCTYPE(P, P, ctypes.c_size_t, P)
+_FREE_FN = ctypes.CFUNCTYPE(None, P, P, P)
+
+
+class dot_allocator(ctypes.Structure):
+    _fields_ = [("ctx", P), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+class dot_primitive(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int64), ("p", ctypes.c_int64 * 7)]
+
+
+class dot_build_desc(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_float * 3), ("half_size", ctypes.c_float),
+                ("max_depth", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("n_primitives", ctypes.c_int32),
+                ("primitives", P), ("density_lo", ctypes.c_float), ("density_hi", ctypes.c_float),
+                ("sh_std", ctypes.c_float), ("sh_dc", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class dot_tree_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("max_level", ctypes.c_int32), ("sh_degree", ctypes.c_int32),
+                ("n_coeffs", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("sh_row_stride", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("center", ctypes.c_float * 3), ("half_size", ctypes.c_float),
+                ("child", P), ("node_parent", P), ("node_key", P), ("leaf_parent", P),
+                ("leaf_key", P), ("sigma", P), ("sh", P)]
+
+
+class dot_host_tree(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("sh_degree", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("center", ctypes.c_float * 3), ("half_size", ctypes.c_float),
+                ("child", P), ("node_parent", P), ("node_key", P), ("leaf_parent", P),
+                ("leaf_key", P), ("sigma", P), ("sh", P)]
+
+
+class dot_camera(ctypes.Structure):
+    _fields_ = [("c2w", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class dot_rays(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_cameras", ctypes.c_int32), ("cameras", P),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_rays", ctypes.c_int64),
+                ("origins", P), ("dirs", P)]
+
+
+class dot_render_opts(ctypes.Structure):
+    _fields_ = [("background", ctypes.c_float * 3), ("eps_T", ctypes.c_float),
+                ("color_act", ctypes.c_int32), ("signal_mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_steps", ctypes.c_int32)]
+
+
+class dot_select_opts(ctypes.Structure):
+    _fields_ = [("prune_mode", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
+                ("prune_value", ctypes.c_double), ("sample_value", ctypes.c_double)]
+
+
+class dot_refine_counts(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_pruned_groups", ctypes.c_int64), ("n_sampled", ctypes.c_int64),
+                ("n_capped", ctypes.c_int64)]
+
+
+class dot_leaf_array(ctypes.Structure):
+    _fields_ = [("src", P), ("dst", P), ("width", ctypes.c_int32), ("merge", ctypes.c_int32)]
+
+
+assert ctypes.sizeof(dot_camera) == 72 and ctypes.sizeof(dot_primitive) == 64
+
+# ----------------------------------------------------------------------------------------------
+# library loading
+# ----------------------------------------------------------------------------------------------
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libdot (built in-tree first if missing or stale); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    L.dot_last_error.restype = ctypes.c_char_p
+    L.dot_last_error.argtypes = []
+    L.dot_version.restype = ctypes.c_int
+    L.dot_version.argtypes = []
+    sigs = {
+        "dot_octree_build": [ctypes.POINTER(dot_build_desc), ctypes.POINTER(dot_allocator), P, ctypes.POINTER(P)],
+        "dot_tree_free": [P],
+        "dot_tree_get_info": [P, ctypes.POINTER(dot_tree_info)],
+        "dot_tree_export": [P, P, P, P, P, P, P, P, P],
+        "dot_tree_import": [ctypes.POINTER(dot_host_tree), ctypes.POINTER(dot_allocator), P, ctypes.POINTER(P)],
+        "dot_tree_status": [P, P, ctypes.POINTER(ctypes.c_uint32)],
+        "dot_render_forward": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), P, P, P, P],
+        "dot_render_backward": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), P, P, P, P, P, P],
+        "dot_accumulate_signal": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.c_int32, P, P],
+        "dot_select_masks": [P, P, ctypes.POINTER(dot_select_opts), P, P, P],
+        "dot_refine_plan": [P, P, P, ctypes.c_int32, ctypes.POINTER(dot_refine_counts), P],
+        "dot_refine_prune": [P, P, P, ctypes.c_int32, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
+        "dot_render_stats": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.POINTER(ctypes.c_int64), P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != DOT_OK:
+        raise DotError(rc, lib().dot_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if isinstance(stream, int) and stream == 0:
+        return ctypes.c_void_p(None)            # the legacy default stream
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, numel=None, name="tensor"):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+
+
+class _CAI:
+    """A device buffer exposed through __cuda_array_interface__ (zero-copy torch view)."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "strides": None, "version": 3}
+        self._owner = owner
+
+
+def _view(ptr: int, shape, dtype: torch.dtype, owner) -> torch.Tensor:
+    if int(np.prod(shape)) == 0:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    ts = {torch.float32: "<f4", torch.float16: "<f2", torch.bfloat16: "<i2", torch.int32: "<i4",
+          torch.int64: "<i8", torch.uint8: "|u1"}[dtype]
+    t = torch.as_tensor(_CAI(ptr, shape, ts, owner), device="cuda")
+    return t.view(torch.bfloat16) if dtype == torch.bfloat16 else t
+
+
+# ----------------------------------------------------------------------------------------------
+# the tree handle
+# ----------------------------------------------------------------------------------------------
+class Octree:
+    """Owner of a ``dot_tree`` handle.  ``sigma`` / ``sh`` are zero-copy views of the leaf
+    parameters (valid until the next refine or free)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+    def info(self) -> dot_tree_info:
+        inf = dot_tree_info()
+        _check(lib().dot_tree_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def n_leaves(self) -> int:
+        return int(self.info().n_leaves)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.info().n_nodes)
+
+    @property
+    def storage(self) -> int:
+        return int(self.info().storage)
+
+    @property
+    def sh_degree(self) -> int:
+        return int(self.info().sh_degree)
+
+    @property
+    def sigma(self) -> torch.Tensor:
+        inf = self.info()
+        return _view(inf.sigma, (inf.n_leaves,), _TORCH_OF_STORAGE[inf.storage], self)
+
+    @property
+    def sh_rows(self) -> torch.Tensor:
+        """[L, row_stride] padded rows."""
+        inf = self.info()
+        return _view(inf.sh, (inf.n_leaves, inf.sh_row_stride), _TORCH_OF_STORAGE[inf.storage], self)
+
+    @property
+    def sh(self) -> torch.Tensor:
+        """[L, 3, K] view of the SH coefficients."""
+        inf = self.info()
+        K = inf.n_coeffs
+        return self.sh_rows[:, : 3 * K].unflatten(1, (3, K))
+
+    def export(self, stream=None) -> dict:
+        inf = self.info()
+        N, L, K = inf.n_nodes, inf.n_leaves, inf.n_coeffs
+        dt = _NP_OF_STORAGE[inf.storage]
+        out = {"child": np.empty((N, 8), np.int32), "node_parent": np.empty(N, np.int32),
+               "node_key": np.empty(N, np.uint64), "leaf_parent": np.empty(L, np.int32),
+               "leaf_key": np.empty(L, np.uint64), "sigma": np.empty(L, dt),
+               "sh": np.empty((L, 3, K), dt)}
+        _check(lib().dot_tree_export(self.handle, _stream(stream),
+                                     *[out[k].ctypes.data_as(P) for k in
+                                       ("child", "node_parent", "node_key", "leaf_parent",
+                                        "leaf_key", "sigma", "sh")]))
+        out.update(center=tuple(inf.center), half_size=float(inf.half_size),
+                   sh_degree=int(inf.sh_degree), storage=int(inf.storage),
+                   max_level=int(inf.max_level))
+        return out
+
+    def status(self, stream=None) -> int:
+        s = ctypes.c_uint32(0)
+        _check(lib().dot_tree_status(self.handle, _stream(stream), ctypes.byref(s)))
+        return int(s.value)
+
+    def free(self):
+        if self.handle:
+            torch.cuda.synchronize()
+            lib().dot_tree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.dot_tree_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------------------------
+# descriptors
+# ----------------------------------------------------------------------------------------------
+def build_desc(center, half_size, max_depth, sh_degree, storage, prims: np.ndarray,
+               density=(10.0, 200.0), sh_std=0.5, sh_dc=0.5, seed=0):
+    prims = np.ascontiguousarray(prims, dtype=np.int64).reshape(-1, 8)
+    d = dot_build_desc()
+    d.center = (ctypes.c_float * 3)(*[float(x) for x in center])
+    d.half_size = float(half_size)
+    d.max_depth = int(max_depth)
+    d.sh_degree = int(sh_degree)
+    d.storage = int(storage)
+    d.n_primitives = prims.shape[0]
+    d.primitives = prims.ctypes.data_as(P) if prims.shape[0] else None
+    d.density_lo, d.density_hi = float(density[0]), float(density[1])
+    d.sh_std, d.sh_dc = float(sh_std), float(sh_dc)
+    d.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    d._keep = prims
+    return d
+
+
+def render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4, color_act=DOT_ACT_SIGMOID,
+                signal_mode=DOT_SIGNAL_NONE, precision=DOT_PRECISION_AUTO, max_steps=0):
+    o = dot_render_opts()
+    o.background = (ctypes.c_float * 3)(*[float(x) for x in background])
+    o.eps_T = float(eps_T)
+    o.color_act = int(color_act)
+    o.signal_mode = int(signal_mode)
+    o.precision = int(precision)
+    o.max_steps = int(max_steps)
+    return o
+
+
+def rays_buffer(origins: torch.Tensor, dirs: torch.Tensor) -> dot_rays:
+    _need(origins, torch.float32, name="origins")
+    _need(dirs, torch.float32, origins.numel(), name="dirs")
+    r = dot_rays()
+    r.kind = DOT_RAYS_BUFFER
+    r.n_rays = origins.numel() // 3
+    r.origins = _ptr(origins)
+    r.dirs = _ptr(dirs)
+    r._keep = (origins, dirs)
+    return r
+
+
+def cameras_tensor(cams: Sequence, device="cuda") -> torch.Tensor:
+    """float32 [n, 18] device tensor of dot_camera records from seeded_inputs-style cameras."""
+    arr = np.stack([c.packed() for c in cams]).astype(np.float32)
+    return torch.from_numpy(arr).to(device)
+
+
+def rays_cameras(cams: torch.Tensor, width: int, height: int) -> dot_rays:
+    _need(cams, torch.float32, name="cameras")
+    if cams.dim() != 2 or cams.shape[1] != 18:
+        raise ValueError("cameras must be [n, 18] float32 records")
+    r = dot_rays()
+    r.kind = DOT_RAYS_CAMERAS
+    r.n_cameras = cams.shape[0]
+    r.cameras = _ptr(cams)
+    r.width, r.height = int(width), int(height)
+    r.n_rays = 0
+    r._keep = cams
+    return r
+
+
+def n_rays_of(r: dot_rays) -> int:
+    if r.kind == DOT_RAYS_BUFFER:
+        return int(r.n_rays)
+    return int(r.n_cameras) * int(r.width) * int(r.height)
+
+
+def select_opts(prune_mode=DOT_SELECT_NONE, prune_value=0.0, sample_mode=DOT_SELECT_NONE,
+                sample_value=0.0):
+    o = dot_select_opts()
+    o.prune_mode, o.sample_mode = int(prune_mode), int(sample_mode)
+    o.prune_value, o.sample_value = float(prune_value), float(sample_value)
+    return o
+
+
+# ----------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------------------------
+def dot_version() -> int:
+    return int(lib().dot_version())
+
+
+def dot_last_error() -> str:
+    return lib().dot_last_error().decode()
+
+
+def dot_octree_build(desc: dot_build_desc, stream=None) -> Octree:
+    h = ctypes.c_void_p()
+    _check(lib().dot_octree_build(ctypes.byref(desc), None, _stream(stream), ctypes.byref(h)))
+    return Octree(h)
+
+
+def dot_tree_import(host: dict, stream=None) -> Octree:
+    """Tree from host arrays (keys child, node_parent, node_key, leaf_parent, leaf_key, sigma,
+    sh [L,3,K], center, half_size, sh_degree, storage)."""
+    keep = {k: np.ascontiguousarray(host[k]) for k in
+            ("child", "node_parent", "node_key", "leaf_parent", "leaf_key", "sigma", "sh")}
+    h = dot_host_tree()
+    h.n_nodes = keep["node_key"].shape[0]
+    h.n_leaves = keep["leaf_key"].shape[0]
+    h.sh_degree = int(host["sh_degree"])
+    h.storage = int(host["storage"])
+    h.center = (ctypes.c_float * 3)(*[float(x) for x in host["center"]])
+    h.half_size = float(host["half_size"])
+    for k, v in keep.items():
+        setattr(h, k, v.ctypes.data_as(P))
+    out = ctypes.c_void_p()
+    _check(lib().dot_tree_import(ctypes.byref(h), None, _stream(stream), ctypes.byref(out)))
+    return Octree(out)
+
+
+def dot_render_forward(tree: Octree, rays: dot_rays, opts: dot_render_opts, rgb: torch.Tensor,
+                       T_final: Optional[torch.Tensor] = None,
+                       signal: Optional[torch.Tensor] = None, stream=None):
+    R = n_rays_of(rays)
+    _need(rgb, torch.float32, 3 * R, "rgb")
+    if T_final is not None:
+        _need(T_final, torch.float32, R, "T_final")
+    if signal is not None:
+        _need(signal, torch.float32, tree.n_leaves, "signal")
+    _check(lib().dot_render_forward(tree.handle, ctypes.byref(rays), ctypes.byref(opts), _ptr(rgb),
+                                    _ptr(T_final), _ptr(signal), _stream(stream)))
+
+
+def dot_render_backward(tree: Octree, rays: dot_rays, opts: dot_render_opts,
+                        grad_rgb: torch.Tensor, rgb: torch.Tensor, grad_sigma: torch.Tensor,
+                        grad_sh: torch.Tensor, signal: Optional[torch.Tensor] = None, stream=None):
+    R = n_rays_of(rays)
+    inf = tree.info()
+    _need(grad_rgb, torch.float32, 3 * R, "grad_rgb")
+    _need(rgb, torch.float32, 3 * R, "rgb")
+    _need(grad_sigma, torch.float32, inf.n_leaves, "grad_sigma")
+    _need(grad_sh, torch.float32, inf.n_leaves * 3 * inf.n_coeffs, "grad_sh")
+    if signal is not None:
+        _need(signal, torch.float32, inf.n_leaves, "signal")
+    _check(lib().dot_render_backward(tree.handle, ctypes.byref(rays), ctypes.byref(opts),
+                                     _ptr(grad_rgb), _ptr(rgb), _ptr(grad_sigma), _ptr(grad_sh),
+                                     _ptr(signal), _stream(stream)))
+
+
+def dot_accumulate_signal(tree: Octree, rays: Optional[dot_rays], opts: dot_render_opts,
+                          mode: int, signal: torch.Tensor, stream=None):
+    _need(signal, torch.float32, tree.n_leaves, "signal")
+    rp = ctypes.byref(rays) if rays is not None else None
+    _check(lib().dot_accumulate_signal(tree.handle, rp, ctypes.byref(opts), int(mode),
+                                       _ptr(signal), _stream(stream)))
+
+
+def dot_select_masks(tree: Octree, signal: torch.Tensor, opts: dot_select_opts,
+                     prune_mark: torch.Tensor, sample_mark: torch.Tensor, stream=None):
+    L = tree.n_leaves
+    _need(signal, torch.float32, L, "signal")
+    _need(prune_mark, torch.uint8, L, "prune_mark")
+    _need(sample_mark, torch.uint8, L, "sample_mark")
+    _check(lib().dot_select_masks(tree.handle, _ptr(signal), ctypes.byref(opts), _ptr(prune_mark),
+                                  _ptr(sample_mark), _stream(stream)))
+
+
+def dot_refine_plan(tree: Octree, prune_mark: torch.Tensor, sample_mark: torch.Tensor,
+                    depth_cap: int, stream=None) -> dict:
+    L = tree.n_leaves
+    _need(prune_mark, torch.uint8, L, "prune_mark")
+    _need(sample_mark, torch.uint8, L, "sample_mark")
+    c = dot_refine_counts()
+    _check(lib().dot_refine_plan(tree.handle, _ptr(prune_mark), _ptr(sample_mark), int(depth_cap),
+                                 ctypes.byref(c), _stream(stream)))
+    return {k: int(getattr(c, k)) for k, _ in dot_refine_counts._fields_}
+
+
+def dot_refine_prune(tree: Octree, prune_mark: torch.Tensor, sample_mark: torch.Tensor,
+                     depth_cap: int, leaf_map: torch.Tensor,
+                     aux: Sequence = (), stream=None):
+    """aux: sequence of (src [L_old, w] f32, dst [L_new, w] f32, merge) tensors / modes."""
+    L = tree.n_leaves
+    _need(prune_mark, torch.uint8, L, "prune_mark")
+    _need(sample_mark, torch.uint8, L, "sample_mark")
+    _need(leaf_map, torch.int32, None, "leaf_map")
+    arr = (dot_leaf_array * max(1, len(aux)))()
+    for i, (src, dst, merge) in enumerate(aux):
+        w = src.numel() // L if L else 1
+        _need(src, torch.float32, L * w, "aux src")
+        _need(dst, torch.float32, None, "aux dst")
+        arr[i].src, arr[i].dst, arr[i].width, arr[i].merge = src.data_ptr(), dst.data_ptr(), w, int(merge)
+    _check(lib().dot_refine_prune(tree.handle, _ptr(prune_mark), _ptr(sample_mark), int(depth_cap),
+                                  _ptr(leaf_map), arr, len(aux), _stream(stream)))
+
+
+def dot_render_stats(tree: Octree, rays: dot_rays, opts: dot_render_opts, stream=None):
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().dot_render_stats(tree.handle, ctypes.byref(rays), ctypes.byref(opts), out,
+                                  _stream(stream)))
+    return {"rays_hit": out[0], "segments": out[1], "occupied": out[2], "child_loads": out[3]}
+
+
+def dot_tree_status(tree: Octree, stream=None) -> int:
+    return tree.status(stream)

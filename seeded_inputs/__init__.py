@@ -213,7 +213,7 @@ def splitmix64(seed: int, counter: np.ndarray) -> np.ndarray:
 def irwin_hall_scale(sh_std: float) -> np.float32:
     """float32 factor turning the centred Irwin-Hall integer (see leaf_params) into N(0, sh_std)."""
     s_ih = 2.0 * math.sqrt(4.0 * (65536.0 * 65536.0 - 1.0) / 12.0)
-    return np.float32(sh_std / s_ih)
+    return np.float32(float(np.float32(sh_std)) / s_ih)     # the std as a float32 parameter
 
 
 def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:

@@ -1,0 +1,67 @@
+"""GPU octree build vs the oracle: structure bit-exact, seeded parameters bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from helpers import bits, oracle_side
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    si.tiny_sphere_scene(),
+    si.random_scene(1, max_depth=5, sh_degree=0, storage=si.STORAGE_F16, n_prims=4),
+    si.random_scene(2, max_depth=6, sh_degree=2, storage=si.STORAGE_BF16, n_prims=5),
+    si.random_scene(3, max_depth=4, sh_degree=3, storage=si.STORAGE_F32, n_prims=3),
+    si.box_scene((-2, -2, -2), (2, 2, 2), max_depth=3),            # every cell subdivided
+    si.box_scene((5, 5, 5), (6, 6, 6), max_depth=3),               # nothing meets: root + 8 leaves
+]
+
+
+@pytest.mark.parametrize("scene", SMALL, ids=lambda s: f"{s.name}-d{s.max_depth}-s{s.storage}-k{s.sh_degree}")
+def test_build_bit_exact(scene):
+    import paper_2307_15333_gb300 as dot
+    tree = dot.octree_from_scene(scene)
+    ex = tree.export()
+    t, sig, sh, _, _ = oracle_side(scene)
+    for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key"):
+        np.testing.assert_array_equal(ex[k], t[k], err_msg=k)
+    np.testing.assert_array_equal(bits(ex["sigma"]), bits(sig))
+    np.testing.assert_array_equal(bits(ex["sh"]), bits(sh))
+    lv = oracle.key_level(t["leaf_key"])
+    assert ex["max_level"] == int(lv.max())
+    assert tree.status() == 0
+    tree.free()
+
+
+@pytest.mark.parametrize("cfg", ["nerf_synthetic", "tanks_temples"])
+def test_build_full_size(cfg):
+    """Full-size scenes: every structural array bit-exact, parameters on a sample of leaves."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.nerf_synthetic_scene() if cfg == "nerf_synthetic" else si.tanks_temples_scene()
+    tree = dot.octree_from_scene(scene)
+    ex = tree.export()
+    t = oracle.scene_tree(scene)
+    for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key"):
+        np.testing.assert_array_equal(ex[k], t[k], err_msg=k)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([rng.integers(0, t["leaf_key"].size, 50000),
+                                    [0, t["leaf_key"].size - 1]]))
+    sig, sh = si.leaf_params(t["leaf_key"][idx], t["leaf_inside"][idx], scene)
+    np.testing.assert_array_equal(bits(ex["sigma"][idx]), bits(sig))
+    np.testing.assert_array_equal(bits(ex["sh"][idx]), bits(sh))
+    tree.free()
+
+
+def test_import_export_round_trip():
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(4, max_depth=5, sh_degree=1, storage=si.STORAGE_BF16)
+    a = dot.octree_from_scene(scene)
+    ea = a.export()
+    b = dot.dot_tree_import(ea)
+    eb = b.export()
+    for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key", "sigma", "sh"):
+        np.testing.assert_array_equal(bits(ea[k]), bits(eb[k]), err_msg=k)
+    assert ea["max_level"] == eb["max_level"]
+    a.free()
+    b.free()

@@ -1,0 +1,165 @@
+"""GPU forward render (Eq. 1-2) vs the FP64 oracle on the same seeded inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import seeded_inputs as si
+from helpers import assert_pixels_close, oracle_side
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_render(tree, o, d, **kw):
+    import paper_2307_15333_gb300 as dot
+    rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    R = o.shape[0]
+    rgb = torch.empty(R, 3, device="cuda")
+    T = torch.empty(R, device="cuda")
+    dot.dot_render_forward(tree, rays, dot.render_opts(**kw), rgb, T)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), T.cpu().numpy()
+
+
+def test_tiny_config_camera_mode_matches_buffer_mode_and_oracle():
+    import paper_2307_15333_gb300 as dot
+    scene, cams = si.config_tiny()
+    tree = dot.octree_from_scene(scene)
+    cam_t = dot.cameras_tensor(cams)
+    rgb_c = torch.empty(64 * 64, 3, device="cuda")
+    T_c = torch.empty(64 * 64, device="cuda")
+    opts = dot.render_opts(background=(1, 1, 1), eps_T=1e-4)
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 64, 64), opts, rgb_c, T_c)
+    o, d = si.camera_rays(cams[0])
+    rgb_b, T_b = _gpu_render(tree, o, d, background=(1, 1, 1), eps_T=1e-4)
+    # in-kernel ray generation follows the same float32 operations as the input generator
+    np.testing.assert_array_equal(rgb_c.cpu().numpy(), rgb_b)
+    np.testing.assert_array_equal(T_c.cpu().numpy(), T_b)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    ref, Tref, _ = oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, eps_T=1e-4)
+    assert_pixels_close(rgb_b, ref, scene.storage)
+    assert_pixels_close(T_b, Tref, scene.storage, what="T")
+    assert (ref.min() < 0.9) and np.any(Tref < 1e-3)     # the sphere is in view and opaque
+    tree.free()
+
+
+CASES = [(st, deg) for st in (si.STORAGE_F32, si.STORAGE_F16, si.STORAGE_BF16) for deg in range(4)]
+
+
+@pytest.mark.parametrize("storage,deg", CASES)
+def test_random_scene_random_rays(storage, deg):
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(10 + deg, max_depth=6, sh_degree=deg, storage=storage, n_prims=4)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    o, d = si.random_rays(3000, 100 + deg)
+    for eps in (1e-4, 0.0):
+        for act in (dot.dot.DOT_ACT_SIGMOID, dot.dot.DOT_ACT_LINEAR):
+            bg = (0.2, 0.5, 1.0)
+            got, Tg = _gpu_render(tree, o, d, background=bg, eps_T=eps, color_act=act)
+            ref, Tr, _ = oracle.render(t, lo, size, s64, h64, deg, o, d, bg=bg, eps_T=eps,
+                                       color_act=act)
+            assert_pixels_close(got, ref, storage)
+            assert_pixels_close(Tg, Tr, storage, what="T")
+    tree.free()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_precision_modes_on_fp32(precision):
+    """Fast plane times stay within the 16-bit-leaf tolerance on FP32 leaves; exact mode meets
+    the FP32 tolerance."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(31, max_depth=7, sh_degree=2, storage=si.STORAGE_F32, n_prims=5)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    o, d = si.random_rays(4000, 7)
+    got, _ = _gpu_render(tree, o, d, precision=precision)
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, 2, o, d)
+    assert_pixels_close(got, ref, si.STORAGE_F32, exact=(precision == 2))
+    tree.free()
+
+
+def test_edge_cases():
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(5, max_depth=5, sh_degree=1, storage=si.STORAGE_F32)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    # no rays
+    got, _ = _gpu_render(tree, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    assert got.shape == (0, 3)
+    # rays that miss the root, rays starting inside it, exactly axis-aligned rays through cell
+    # faces and centres, and a ray along a root edge
+    o = np.array([[3, 3, 3], [0, 0, 0], [0.1, -0.2, 0.3], [0.0, 0.0, 5.0], [0.125, 0.375, -5.0],
+                  [-1.0, -1.0, 5.0], [0.03125, 0.0, 0.0]], np.float32)
+    d = np.array([[1, 0, 0], [0, 0, 1], [0.6, 0.0, -0.8], [0, 0, -1], [0, 0, 1], [0, 0, -1],
+                  [0, 1, 0]], np.float32)
+    got, Tg = _gpu_render(tree, o, d, background=(0.3, 0.6, 0.9))
+    ref, Tr, _ = oracle.render(t, lo, size, s64, h64, 1, o, d, bg=(0.3, 0.6, 0.9))
+    np.testing.assert_array_equal(got[0], np.float32([0.3, 0.6, 0.9]))
+    assert Tg[0] == 1.0
+    assert_pixels_close(got, ref, si.STORAGE_F32)
+    tree.free()
+
+
+def test_full_size_nerf_synthetic_sampled_pixels():
+    """Config at full size (2.9M leaves, 800x800 views) in the bench's launch configuration
+    (camera mode, all views in one launch); sampled pixels against the oracle."""
+    import paper_2307_15333_gb300 as dot
+    scene, cams = si.config_nerf_synthetic(n_views=100)
+    tree = dot.octree_from_scene(scene)
+    cam_t = dot.cameras_tensor(cams)
+    R = 100 * 800 * 800
+    rgb = torch.empty(R, 3, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 800, 800), dot.render_opts(), rgb)
+    torch.cuda.synchronize()
+    assert tree.status() == 0
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    rng = np.random.default_rng(3)
+    for v in (0, 37, 99):
+        pix = rng.integers(0, 800 * 800, 1500)
+        o, d = si.camera_rays(cams[v], pix)
+        ref, _, _ = oracle.render(t, lo, size, s64, h64, 3, o, d)
+        got = rgb[v * 800 * 800 + torch.from_numpy(pix).cuda()].cpu().numpy()
+        assert_pixels_close(got, ref, scene.storage)
+        assert np.std(ref) > 0.05                       # not a blank view
+    tree.free()
+
+
+def test_full_size_tanks_temples_sampled_pixels():
+    import paper_2307_15333_gb300 as dot
+    scene, cams = si.config_tanks_temples(n_views=6)
+    tree = dot.octree_from_scene(scene)
+    cam_t = dot.cameras_tensor(cams)
+    R = 6 * 1920 * 1080
+    rgb = torch.empty(R, 3, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 1920, 1080), dot.render_opts(), rgb)
+    torch.cuda.synchronize()
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    rng = np.random.default_rng(4)
+    for v in (0, 5):
+        pix = rng.integers(0, 1920 * 1080, 1500)
+        o, d = si.camera_rays(cams[v], pix)
+        ref, _, _ = oracle.render(t, lo, size, s64, h64, 3, o, d)
+        got = rgb[v * 1920 * 1080 + torch.from_numpy(pix).cuda()].cpu().numpy()
+        assert_pixels_close(got, ref, scene.storage)
+    tree.free()
+
+
+def test_step_cap_sets_status_without_hanging():
+    """A per-ray step cap that is too small truncates rays and raises the status bit."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(6, max_depth=6, sh_degree=0, storage=si.STORAGE_F32)
+    tree = dot.octree_from_scene(scene)
+    o, d = si.random_rays(500, 1)
+    _gpu_render(tree, o, d, max_steps=2)
+    assert tree.status() & dot.dot.DOT_STATUS_STEP_LIMIT
+    assert tree.status() == 0                          # read clears it
+    _gpu_render(tree, o, d)
+    assert tree.status() == 0
+    tree.free()
