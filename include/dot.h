@@ -276,6 +276,33 @@ int dot_select_masks(const dot_tree *tree, const float *signal, const dot_select
                      uint8_t *prune_mark, uint8_t *sample_mark, void *stream);
 
 /*
+ * dot_select_masks_noalloc -- the same prune and sample marks as dot_select_masks, computed
+ * without allocating any device memory.  The paper has no counterpart to this call.
+ *
+ * It exists for applications that cannot have the library allocate while it works: a process
+ * that reserves its whole device-memory budget at start-up (an engine or renderer that owns the
+ * memory pool, or a serving loop that admits work by free memory and must not see hidden
+ * allocations shift that figure), or a caller whose allocation path may block or fail while the
+ * device is under memory pressure.  dot_select_masks takes its working memory from
+ * cudaMallocAsync; this call never calls cudaMalloc, cudaMallocAsync, cudaFree or any other
+ * allocating routine.
+ *
+ * Its working memory is one fixed array of about 66 KB in the library's device memory (the
+ * radix-select histogram and state, and one count per tile of 4096 leaves), which every GPU
+ * that loads the library keeps until the process exits.  Limits and behaviour:
+ *  - trees of at most 2^26 (67,108,864) leaves; larger trees return DOT_ERR_INVALID_ARG;
+ *  - the first call on each device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture;
+ *  - every call on a device shares the array and leaves its last contents there (the call clears
+ *    what must start at zero itself); calls whose work overlaps on the GPU, for example on two
+ *    streams without ordering, race on it and can return wrong marks, so order such calls.
+ * Arguments, modes, tie-breaking and results are those of dot_select_masks.
+ */
+int dot_select_masks_noalloc(const dot_tree *tree, const float *signal,
+                             const dot_select_opts *opts, uint8_t *prune_mark,
+                             uint8_t *sample_mark, void *stream);
+
+/*
  * dot_refine_plan -- the sizes dot_refine_prune will produce for these marks (synchronises).
  */
 int dot_refine_plan(const dot_tree *tree, const uint8_t *prune_mark, const uint8_t *sample_mark,

@@ -556,3 +556,35 @@ int dot_render_stats(const dot_tree *t, const dot_rays *rays, const dot_render_o
 }
 
 }  // extern "C"
+
+namespace dot {
+int64_t select_noalloc_max_leaves();
+cudaError_t select_masks_noalloc(const float *signal, int64_t n, int prune_mode,
+                                 double prune_value, int sample_mode, double sample_value,
+                                 uint8_t *prune_mark, uint8_t *sample_mark, cudaStream_t s);
+}  // namespace dot
+
+extern "C" int dot_select_masks_noalloc(const dot_tree *t, const float *signal,
+                                        const dot_select_opts *opts, uint8_t *prune_mark,
+                                        uint8_t *sample_mark, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    const int64_t L = t->a.n_leaves;
+    if (L > dot::select_noalloc_max_leaves())
+        return fail(DOT_ERR_INVALID_ARG,
+                    "dot_select_masks_noalloc handles at most 2^26 leaves; use dot_select_masks");
+    for (int m : {opts->prune_mode, opts->sample_mode})
+        if (m < DOT_SELECT_NONE || m > DOT_SELECT_FRACTION)
+            return fail(DOT_ERR_INVALID_ARG, "unknown selection mode");
+    if ((opts->prune_mode == DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
+        (opts->sample_mode == DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
+        return fail(DOT_ERR_INVALID_ARG, "selection fraction must be in [0, 1]");
+    if (L > 0 && (!signal || !prune_mark || !sample_mark))
+        return fail(DOT_ERR_INVALID_ARG, "signal and masks must not be NULL");
+    API_CK(dot::select_masks_noalloc(signal, L, opts->prune_mode, opts->prune_value,
+                                     opts->sample_mode, opts->sample_value, prune_mark,
+                                     sample_mark, S(stream)),
+           "dot_select_masks_noalloc");
+    return DOT_OK;
+}

@@ -37,7 +37,8 @@ DOT_STATUS_STEP_LIMIT = 1
 ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_free",
                 "dot_tree_get_info", "dot_tree_export", "dot_tree_import", "dot_tree_status",
                 "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
-                "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats")
+                "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
+                "dot_select_masks_noalloc")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -160,6 +161,7 @@ def lib() -> ctypes.CDLL:
         "dot_refine_plan": [P, P, P, ctypes.c_int32, ctypes.POINTER(dot_refine_counts), P],
         "dot_refine_prune": [P, P, P, ctypes.c_int32, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
         "dot_render_stats": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.POINTER(ctypes.c_int64), P],
+        "dot_select_masks_noalloc": [P, P, ctypes.POINTER(dot_select_opts), P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -463,6 +465,18 @@ def dot_select_masks(tree: Octree, signal: torch.Tensor, opts: dot_select_opts,
     _need(sample_mark, torch.uint8, L, "sample_mark")
     _check(lib().dot_select_masks(tree.handle, _ptr(signal), ctypes.byref(opts), _ptr(prune_mark),
                                   _ptr(sample_mark), _stream(stream)))
+
+
+def dot_select_masks_noalloc(tree: Octree, signal: torch.Tensor, opts: dot_select_opts,
+                             prune_mark: torch.Tensor, sample_mark: torch.Tensor, stream=None):
+    """dot_select_masks without any device allocation (for callers that must not allocate);
+    trees of at most 2^26 leaves, and overlapping calls on one device must be ordered."""
+    L = tree.n_leaves
+    _need(signal, torch.float32, L, "signal")
+    _need(prune_mark, torch.uint8, L, "prune_mark")
+    _need(sample_mark, torch.uint8, L, "sample_mark")
+    _check(lib().dot_select_masks_noalloc(tree.handle, _ptr(signal), ctypes.byref(opts),
+                                          _ptr(prune_mark), _ptr(sample_mark), _stream(stream)))
 
 
 def dot_refine_plan(tree: Octree, prune_mark: torch.Tensor, sample_mark: torch.Tensor,
