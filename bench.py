@@ -37,13 +37,15 @@ BATCH = 1 << 16
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="dot", choices=["dot", "reference"])
     p.add_argument("--views", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=1000,
+                   help="requests per serving trace at 200 req/s (twice as many at 2000 req/s)")
     return p.parse_args()
 
 
@@ -147,15 +149,19 @@ def oracle_baseline(scene, cams, budget_s: float, threads: int):
     s64, h64 = si.storage_to_f64(sig, scene.storage), si.storage_to_f64(sh, scene.storage)
     lo, size = oracle.root_of(scene)
     W, H = cams[0].width, cams[0].height
-    # calibrate on a small sample, then size the measured sample to the time budget
-    stride = 4093
-    pix = np.arange(0, W * H, stride)
-    o, d = si.camera_rays(cams[0], pix)
-    t0 = time.perf_counter()
-    oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
-    dt = max(time.perf_counter() - t0, 1e-6)
+    # calibrate on growing samples (until one takes a second), then size the measured sample
+    stride = 4096
+    while True:
+        pix = np.arange(0, W * H, stride)
+        o, d = si.camera_rays(cams[0], pix)
+        t0 = time.perf_counter()
+        oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
+        dt = max(time.perf_counter() - t0, 1e-6)
+        if dt > 1.0 or stride == 1:
+            break
+        stride = max(1, stride // 4)
     rate = len(pix) / dt
-    n_views = min(len(cams), 10)
+    n_views = len(cams)
     want = max(1000, int(rate * budget_s))
     stride = max(1, (W * H * n_views) // want)
     os_, ds_ = [], []
@@ -171,6 +177,41 @@ def oracle_baseline(scene, cams, budget_s: float, threads: int):
     return {"value": o.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
             "sample": f"every {stride}th pixel of the first {n_views} 800x800 views "
                       f"({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
+
+
+def measure_serving(args):
+    """Continuous batching (slot tables replayed as CUDA graphs, two in flight) against one
+    launch per request, on the same seeded Poisson traces over four resident trees."""
+    import torch
+
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300 import serve
+    scenes, poses = si.config_serving()
+    trees = [dot.octree_from_scene(s) for s in scenes]
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    free, _ = torch.cuda.mem_get_info()
+    pool_floats = int(min(free // 8, 1 << 28))            # admission pool: an eighth of free HBM
+    res = {"trees": [s.name for s in scenes], "leaves": [t.n_leaves for t in trees],
+           "resolutions": si.SERVE_RESOLUTIONS, "pool_MB": pool_floats * 4 / 1e6,
+           "latency": "arrival to completion observed by the host loop"}
+    for rate, n in ((200.0, args.serve_requests), (2000.0, 2 * args.serve_requests)):
+        row = {}
+        for mode, cls in (("batched", serve.BatchedServer), ("plain", serve.PlainServer)):
+            srv = cls(trees, opts, pool_floats)
+            srv.run(serve.poisson_trace(50, rate, 4, si.SERVE_RESOLUTIONS, poses, seed=1))
+            trace = serve.poisson_trace(n, rate, 4, si.SERVE_RESOLUTIONS, poses, seed=2)
+            torch.cuda.synchronize()
+            srv.run(trace)
+            rays = sum(r.width * r.height for r in trace)
+            span = max(r.done for r in trace) - trace[0].arrival
+            row[mode] = dict(serve.percentiles(trace), mrays_s=rays / span / 1e6, requests=n)
+            del srv
+            torch.cuda.synchronize()
+        res[f"rate_{int(rate)}_per_s"] = row
+    for t in trees:
+        t.free()
+    return res
 
 
 # ----------------------------------------------------------------------------------------------
@@ -284,7 +325,7 @@ def run_dot(args):
     brgb = torch.empty(BATCH, 3, device="cuda")
     gs = torch.zeros(L, device="cuda")
     gsh = torch.zeros(L, 3, K, device="cuda")
-    pairs = max(50, 5 * args.steps)
+    pairs = max(200, 2 * args.steps)
     for i in range(3 * nb):
         r = batches[i % nb]
         dot.dot_render_forward(tree, r, opts, brgb)
@@ -306,6 +347,25 @@ def run_dot(args):
                "batch_rays": BATCH, "pairs": pairs, "ms_per_pair": fb_ms / pairs,
                "grad": "fixed synthetic dL/dC; FP32 gradients accumulate across pairs",
                "clocks": clk2}
+
+    # ---- forward + backward over all views in one batch (64 M rays per pair) ----
+    gfull = torch.full((R, 3), 1e-6, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        dot.dot_render_forward(tree, rays, opts, rgb)
+        dot.dot_render_backward(tree, rays, opts, gfull, rgb, gs, gsh)
+    torch.cuda.synchronize()
+    full_pairs = 5
+    e0.record(stream)
+    for _ in range(full_pairs):
+        dot.dot_render_forward(tree, rays, opts, rgb)
+        dot.dot_render_backward(tree, rays, opts, gfull, rgb, gs, gsh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ff_ms = max_over_ranks(e0.elapsed_time(e1))
+    fwd_bwd["full_batch"] = {"value": R * full_pairs * ws / (ff_ms / 1e3) / 1e6,
+                             "unit": "Mrays/s", "batch_rays": R, "pairs": full_pairs,
+                             "ms_per_pair": ff_ms / full_pairs}
+    del gfull
 
     # ---- end to end through host buffers (pinned cameras in, pinned images out) ----
     cams_host = cam_t.cpu().pin_memory()
@@ -339,6 +399,8 @@ def run_dot(args):
     refine = {"ms": refine_ms, "leaves_before": L, "leaves_after": counts["n_leaves"],
               "signal": f"MAX_WEIGHT over {nb} x 2^16 rays", "select": "bottom 20% / top 5%"}
 
+    serve_res = measure_serving(args) if rank == 0 else None
+
     hbm, peak_kind = peaks()
     achieved = alg_bytes / mean_launch_s / 1e9
     traffic = profiled_traffic("render_fwd_nerf_synthetic_800")
@@ -365,7 +427,7 @@ def run_dot(args):
                              "vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6),
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine,
+            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "serve": serve_res,
             "wall_s_timed": t_wall}
     if rank == 0:
         print(json.dumps(line))

@@ -166,6 +166,25 @@ typedef struct {
     const float *dirs;         /* BUFFER: device [n_rays][3], unit length */
 } dot_rays;
 
+#define DOT_MAX_SERVE_TREES 8
+
+/* One admitted request of a slot table (96 bytes): a camera (its own width and height), the
+ * index of the tree it looks at, its first work tile, and its device output [height][width][3]. */
+typedef struct {
+    dot_camera camera;
+    int32_t tree;
+    int32_t pad_;
+    int64_t tile_begin; /* sum of ceil(W/16) ceil(H/16) over the slots before this one */
+    float *out;
+} dot_slot;
+
+/* A slot table in device memory is this header followed by max_slots dot_slot records. */
+typedef struct {
+    int32_t n_slots;
+    int32_t pad_;
+    int64_t total_tiles; /* tile_begin of the last slot plus its tile count */
+} dot_slot_table_header;
+
 typedef struct {
     float background[3];  /* added as T_final * background */
     float eps_T;          /* stop after the segment that takes T below eps_T; 0 disables; < 1 */
@@ -246,6 +265,20 @@ int dot_tree_status(dot_tree *tree, void *stream, uint32_t *status);
  */
 int dot_render_forward(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
                        float *rgb, float *T_final, float *signal, void *stream);
+
+/*
+ * dot_render_slots -- renders every request of a device slot table in one persistent launch
+ * (Eq. 1-2 per pixel, as dot_render_forward): the requests may differ in resolution and in the
+ * tree they look at.  Blocks take 16x16 tiles from a work counter until the table's tiles run out;
+ * each pixel's value does not depend on the other requests in the table.
+ * trees[n_trees] (1..DOT_MAX_SERVE_TREES, host array of handles): resident trees sharing one
+ * storage type and SH degree.  table: device dot_slot_table_header + max_slots dot_slot (read by
+ * the kernel, so it may be rewritten between launches).  work_counter: device uint64, zeroed by
+ * this call on the stream.  opts->signal_mode must be NONE.
+ */
+int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const void *table,
+                     int32_t max_slots, const dot_render_opts *opts,
+                     unsigned long long *work_counter, void *stream);
 
 /*
  * dot_render_backward -- gradient of L = sum_r grad_rgb[r] . rgb[r] with respect to the leaf

@@ -588,3 +588,40 @@ extern "C" int dot_select_masks_noalloc(const dot_tree *t, const float *signal,
            "dot_select_masks_noalloc");
     return DOT_OK;
 }
+
+namespace dot {
+cudaError_t launch_render_slots(int storage, int deg, bool exact, const TreeView *views,
+                                int n_trees, const void *table, int32_t max_slots,
+                                const RenderParams &rp, unsigned long long *counter,
+                                uint32_t *status, int grid, cudaStream_t s);
+}  // namespace dot
+
+extern "C" int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const void *table,
+                                int32_t max_slots, const dot_render_opts *opts,
+                                unsigned long long *work_counter, void *stream) {
+    if (!trees || n_trees < 1 || n_trees > DOT_MAX_SERVE_TREES)
+        return fail(DOT_ERR_INVALID_ARG, "n_trees must be in [1, DOT_MAX_SERVE_TREES]");
+    if (!table || !work_counter || max_slots < 1)
+        return fail(DOT_ERR_INVALID_ARG, "table, work_counter and max_slots >= 1 are required");
+    dot::TreeView views[DOT_MAX_SERVE_TREES];
+    int max_level = 0;
+    for (int i = 0; i < n_trees; i++) {
+        int rc = check_tree(trees[i]);
+        if (rc) return rc;
+        if (trees[i]->a.storage != trees[0]->a.storage || trees[i]->a.sh_degree != trees[0]->a.sh_degree)
+            return fail(DOT_ERR_INVALID_ARG, "served trees must share storage type and SH degree");
+        views[i] = view_of(trees[i]);
+        if (trees[i]->a.max_level > max_level) max_level = trees[i]->a.max_level;
+    }
+    dot::RenderParams rp;
+    bool exact = false;
+    int rc = make_params(trees[0], opts, rp, exact);
+    if (rc) return rc;
+    if (rp.signal_mode != DOT_SIGNAL_NONE) return fail(DOT_ERR_INVALID_ARG, "signal_mode must be NONE");
+    if (opts->max_steps == 0) rp.max_steps = 3 * (1 << max_level) + 64;
+    API_CK(dot::launch_render_slots(trees[0]->a.storage, trees[0]->a.sh_degree, exact, views,
+                                    n_trees, table, max_slots, rp, work_counter, trees[0]->status,
+                                    0, S(stream)),
+           "dot_render_slots");
+    return DOT_OK;
+}

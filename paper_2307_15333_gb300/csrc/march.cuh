@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+
 #include "internal.cuh"
 
 namespace dot {
@@ -245,17 +246,9 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
 
     const S *sigma = reinterpret_cast<const S *>(tv.sigma);
     const S *shp = reinterpret_cast<const S *>(tv.sh);
-    PT t = tn;
-    int32_t node = 0;
-    int level = 0;
-    int steps = 0;
-    while (true) {
-        if (steps >= rp.max_steps) {
-            atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
-            break;
-        }
-        ++steps;
-        // descend from (node, level) to the leaf holding gc
+
+    // descend from (node, level) to the leaf holding gc, recording the path on the stack
+    auto descend = [&](int32_t node, int level, int32_t &leaf_out, int &level_out) -> bool {
         int32_t c;
         while (true) {
             const int sh = kGridBits - 1 - level;
@@ -267,11 +260,29 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             if (c < 0 || level >= tv.max_level) break;
             node = c;
         }
-        if (c >= 0) {  // deeper than the tree claims: corrupted table, stop the ray
+        leaf_out = -1 - c;
+        level_out = level;
+        return c < 0;  // false: deeper than the tree claims (corrupted table)
+    };
+
+    PT t = tn;
+    int32_t leaf;
+    int level;
+    int steps = 0;
+    if (!descend(0, 0, leaf, level)) {
+        atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
+        level = -1;
+    }
+    // Two-stage pipeline per step: the current leaf's density is requested first; the exit face,
+    // the next cell and the next leaf's descent are computed while that load is in flight; then
+    // the current segment is shaded.
+    while (level >= 0) {
+        if (steps >= rp.max_steps) {
             atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
             break;
         }
-        const int32_t leaf = -1 - c;
+        ++steps;
+        const float sv = Storage<S>::load(sigma + leaf);
         const int cs = 1 << (kGridBits - level);
         int lo_g[3];
         PT te[3];
@@ -290,70 +301,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (!(val(tout) < pinf<float>())) break;  // only for a zero direction
         const float delta = diff(tout, t);
 
-        if constexpr (MODE == kStats) out.st[1] += 1;
-        bool stop = false;
-        if (delta > 0.f) {
-            const float sv = Storage<S>::load(sigma + leaf);
-            if (sv > 0.f) {
-                if constexpr (MODE == kStats) out.st[2] += 1;
-                const float e = ex<EXACT>(-(sv * delta));
-                const float alpha = 1.f - e;
-                const float w = T * alpha;
-                if constexpr (MODE == kFwd || MODE == kBwd) {
-                    float z[3], col[3];
-                    leaf_z<S, K>(shp + (int64_t)leaf * tv.row_stride, Y, z);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ch++)
-                        col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
-                    if constexpr (MODE == kBwd) {
-                        const float Tn = T * e;
-                        float acc = 0.f;
-                        float dz[3];
-#pragma unroll
-                        for (int ch = 0; ch < 3; ch++) {
-                            const float suffix = rgbf[ch] - C[ch];
-                            acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
-                            const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
-                            dz[ch] = g[ch] * w * ag;
-                        }
-                        atomicAdd(io.grad_sigma + leaf, delta * acc);
-                        float *gr = io.grad_sh + (int64_t)leaf * (3 * K);
-                        if constexpr ((3 * K) % 4 == 0) {
-                            if (io.grad_vec) {
-                                float4 *g4 = reinterpret_cast<float4 *>(gr);
-#pragma unroll
-                                for (int q = 0; q < 3 * K / 4; q++) {
-                                    float4 v;
-                                    v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
-                                    v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
-                                    v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
-                                    v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
-                                    atomicAdd(g4 + q, v);
-                                }
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                            }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                        }
-                    }
-                }
-                if (MODE != kStats && io.signal != nullptr) {
-                    if (rp.signal_mode == DOT_SIGNAL_SUM_ALPHA) atomicAdd(io.signal + leaf, alpha);
-                    else if (rp.signal_mode == DOT_SIGNAL_MAX_WEIGHT)
-                        atomicMax(reinterpret_cast<int *>(io.signal) + leaf, __float_as_int(w));
-                }
-                T = T * e;
-                stop = T < rp.eps_T;
-            }
-        }
-        if (stop) break;
-
-        // ---- next cell ----
+        // ---- next cell and its leaf ----
         bool outside = false;
         const float toutv = val(tout);
 #pragma unroll
@@ -367,11 +315,80 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
                 gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
             }
         }
-        if (outside) break;
+        int32_t next_leaf = 0;
+        int next_level = -1;
+        if (!outside) {
+            const unsigned dbits = (unsigned)((gc[0] ^ lo_g[0]) | (gc[1] ^ lo_g[1]) | (gc[2] ^ lo_g[2]));
+            const int lca = kGridBits - 1 - (31 - __clz(dbits));
+            if (!descend(stack[lca * kMarchThreads], lca, next_leaf, next_level)) {
+                atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
+                next_level = -1;
+            }
+        }
+
+        // ---- shade the current segment ----
+        if constexpr (MODE == kStats) out.st[1] += 1;
+        bool stop = false;
+        if (delta > 0.f && sv > 0.f) {
+            if constexpr (MODE == kStats) out.st[2] += 1;
+            const float e = ex<EXACT>(-(sv * delta));
+            const float alpha = 1.f - e;
+            const float w = T * alpha;
+            if constexpr (MODE == kFwd || MODE == kBwd) {
+                float z[3], col[3];
+                leaf_z<S, K>(shp + (int64_t)leaf * tv.row_stride, Y, z);
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++)
+                    col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
+                if constexpr (MODE == kBwd) {
+                    const float Tn = T * e;
+                    float acc = 0.f;
+                    float dz[3];
+#pragma unroll
+                    for (int ch = 0; ch < 3; ch++) {
+                        const float suffix = rgbf[ch] - C[ch];
+                        acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
+                        const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
+                        dz[ch] = g[ch] * w * ag;
+                    }
+                    atomicAdd(io.grad_sigma + leaf, delta * acc);
+                    float *gr = io.grad_sh + (int64_t)leaf * (3 * K);
+                    if constexpr ((3 * K) % 4 == 0) {
+                        if (io.grad_vec) {
+                            float4 *g4 = reinterpret_cast<float4 *>(gr);
+#pragma unroll
+                            for (int q = 0; q < 3 * K / 4; q++) {
+                                float4 v;
+                                v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
+                                v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
+                                v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
+                                v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
+                                atomicAdd(g4 + q, v);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                    }
+                }
+            }
+            if (MODE != kStats && io.signal != nullptr) {
+                if (rp.signal_mode == DOT_SIGNAL_SUM_ALPHA) atomicAdd(io.signal + leaf, alpha);
+                else if (rp.signal_mode == DOT_SIGNAL_MAX_WEIGHT)
+                    atomicMax(reinterpret_cast<int *>(io.signal) + leaf, __float_as_int(w));
+            }
+            T = T * e;
+            stop = T < rp.eps_T;
+        }
+        if (stop || outside) break;
         if (lt(t, tout)) t = tout;
-        const unsigned dbits = (unsigned)((gc[0] ^ lo_g[0]) | (gc[1] ^ lo_g[1]) | (gc[2] ^ lo_g[2]));
-        level = kGridBits - 1 - (31 - __clz(dbits));
-        node = stack[level * kMarchThreads];
+        leaf = next_leaf;
+        level = next_level;
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) out.rgb[ch] = fmaf(T, rp.bg[ch], C[ch]);
@@ -397,8 +414,11 @@ __device__ __forceinline__ void camera_ray(const dot_camera *cam, int i, int j, 
     for (int a = 0; a < 3; a++) d[a] = __fmul_rn(e[a], inv);
 }
 
-template <typename S, int K, int MODE, bool EXACT>
-__global__ void __launch_bounds__(kMarchThreads)
+// MINB: minimum resident blocks per SM requested from the register allocator.  Launches large
+// enough to fill the GPU several times over run the MINB = 4 build (at most 64 registers, 32
+// warps per SM); small launches, whose time is the longest ray's latency, run MINB = 1.
+template <typename S, int K, int MODE, bool EXACT, int MINB>
+__global__ void __launch_bounds__(kMarchThreads, MINB)
 march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
     __shared__ int32_t s_stack[kMaxLevels * kMarchThreads];
     int32_t *stack = s_stack + threadIdx.x;

@@ -13,15 +13,34 @@ inline dim3 march_grid(const RaySource &rs) {
     return dim3((unsigned)((rs.n_rays + kMarchThreads - 1) / kMarchThreads));
 }
 
+// Blocks above which a forward launch uses the occupancy build: two full waves of 4 blocks on
+// every SM of the current device (152 SMs on a GB300).
+inline int64_t occupancy_blocks() {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 2 * 4 * (int64_t)sms;
+}
+
 template <typename S, int K, int MODE>
 cudaError_t launch_sk(bool exact, const TreeView &tv, const RaySource &rs, const RenderParams &rp,
                       const RenderIO &io, cudaStream_t stream) {
     const dim3 grid = march_grid(rs);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    const bool occ = MODE == kFwd && (int64_t)grid.x * grid.y >= occupancy_blocks();
+    if constexpr (MODE == kFwd) {
+        if (occ) {
+            if (exact)
+                march_kernel<S, K, MODE, true, 4><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
+            else
+                march_kernel<S, K, MODE, false, 4><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
+            return cudaGetLastError();
+        }
+    }
     if (exact)
-        march_kernel<S, K, MODE, true><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
+        march_kernel<S, K, MODE, true, 1><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
     else
-        march_kernel<S, K, MODE, false><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
+        march_kernel<S, K, MODE, false, 1><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_tree_get_info", "dot_tree_export", "dot_tree_import", "dot_tree_status",
                 "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
-                "dot_select_masks_noalloc")
+                "dot_select_masks_noalloc", "dot_render_slots")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -162,6 +162,7 @@ def lib() -> ctypes.CDLL:
         "dot_refine_prune": [P, P, P, ctypes.c_int32, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
         "dot_render_stats": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.POINTER(ctypes.c_int64), P],
         "dot_select_masks_noalloc": [P, P, ctypes.POINTER(dot_select_opts), P, P, P],
+        "dot_render_slots": [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.POINTER(dot_render_opts), P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -513,6 +514,18 @@ def dot_render_stats(tree: Octree, rays: dot_rays, opts: dot_render_opts, stream
     _check(lib().dot_render_stats(tree.handle, ctypes.byref(rays), ctypes.byref(opts), out,
                                   _stream(stream)))
     return {"rays_hit": out[0], "segments": out[1], "occupied": out[2], "child_loads": out[3]}
+
+
+def dot_render_slots(trees: Sequence[Octree], table: torch.Tensor, max_slots: int,
+                     opts: dot_render_opts, work_counter: torch.Tensor, stream=None):
+    """One persistent launch over a device slot table (header + max_slots 96-byte slots)."""
+    if not (table.is_cuda and table.numel() * table.element_size() >= 16 + 96 * max_slots):
+        raise ValueError("table must be a device buffer of 16 + 96 * max_slots bytes")
+    if not (work_counter.is_cuda and work_counter.numel() * work_counter.element_size() >= 8):
+        raise ValueError("work_counter must be a device buffer of at least 8 bytes")
+    handles = (ctypes.c_void_p * len(trees))(*[t.handle.value for t in trees])
+    _check(lib().dot_render_slots(handles, len(trees), _ptr(table), int(max_slots),
+                                  ctypes.byref(opts), _ptr(work_counter), _stream(stream)))
 
 
 def dot_tree_status(tree: Octree, stream=None) -> int:

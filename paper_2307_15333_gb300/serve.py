@@ -1,0 +1,286 @@
+"""Serving loop: continuous batching of camera requests over resident octrees.
+
+Requests (a tree, a camera pose, a resolution) arrive over time.  The batched server admits
+waiting requests into free slots whenever a slot table is free and the output pool has room,
+packs them into a slot table (16x16 tiles of every request numbered consecutively), and replays a
+CUDA graph captured once per table: host-to-device copy of the table, then dot_render_slots (one
+persistent launch that drains the tiles of all admitted requests).  Two tables are in flight at
+a time on two streams, so requests that arrive while a batch is on the GPU start in the next one
+at once and their work overlaps on the device.  The plain server launches dot_render_forward once
+per request, in arrival order, on one stream.
+
+Host bookkeeping (pool, packing, trace) is plain Python and runs without a GPU; only
+``BatchedServer`` / ``PlainServer`` touch the device.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import time
+from collections import deque
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+SLOT_BYTES = 96
+HEADER_BYTES = 16
+TILE = 16
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    tree: int
+    width: int
+    height: int
+    camera: np.ndarray          # float32[18] dot_camera record
+    arrival: float              # seconds from the start of the trace
+    offset: int = -1            # float offset of the output in the pool
+    done: float = -1.0          # completion time (seconds from the start)
+
+    @property
+    def floats(self) -> int:
+        return self.width * self.height * 3
+
+    @property
+    def tiles(self) -> int:
+        return ((self.width + TILE - 1) // TILE) * ((self.height + TILE - 1) // TILE)
+
+
+class OutputPool:
+    """First-fit allocator of output images inside one device buffer (offsets in floats)."""
+
+    def __init__(self, capacity_floats: int, align: int = 64):
+        self.capacity = int(capacity_floats)
+        self.align = align
+        self.free = [(0, self.capacity)]          # sorted (start, length)
+
+    def alloc(self, n: int) -> int:
+        n = (n + self.align - 1) // self.align * self.align
+        for i, (s, l) in enumerate(self.free):
+            if l >= n:
+                if l == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (s + n, l - n)
+                return s
+        return -1
+
+    def release(self, start: int, n: int):
+        n = (n + self.align - 1) // self.align * self.align
+        self.free.append((start, n))
+        self.free.sort()
+        merged = []
+        for s, l in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == s:
+                merged[-1] = (merged[-1][0], merged[-1][1] + l)
+            else:
+                merged.append((s, l))
+        self.free = merged
+
+    @property
+    def free_floats(self) -> int:
+        return sum(l for _, l in self.free)
+
+
+def pack_table(reqs: Sequence[Request], pool_base_ptr: int, max_slots: int) -> np.ndarray:
+    """Byte image of a slot table: header then one 96-byte dot_slot per request."""
+    assert len(reqs) <= max_slots
+    buf = np.zeros(HEADER_BYTES + SLOT_BYTES * max_slots, dtype=np.uint8)
+    begin = 0
+    for i, r in enumerate(reqs):
+        rec = buf[HEADER_BYTES + SLOT_BYTES * i: HEADER_BYTES + SLOT_BYTES * (i + 1)]
+        rec[0:72] = np.ascontiguousarray(r.camera, dtype=np.float32).view(np.uint8)
+        rec[72:76] = np.array([r.tree], np.int32).view(np.uint8)
+        rec[80:88] = np.array([begin], np.int64).view(np.uint8)
+        rec[88:96] = np.array([pool_base_ptr + 4 * r.offset], np.uint64).view(np.uint8)
+        begin += r.tiles
+    buf[0:4] = np.array([len(reqs)], np.int32).view(np.uint8)
+    buf[8:16] = np.array([begin], np.int64).view(np.uint8)
+    return buf
+
+
+def poisson_trace(n: int, rate: float, n_trees: int, resolutions, poses, seed: int) -> List[Request]:
+    """n requests with exponential inter-arrival gaps (rate per second), a uniformly drawn tree and
+    resolution, and a camera record from poses(rng, tree, w, h) -> float32[18]."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        tree = int(rng.integers(0, n_trees))
+        w, h = resolutions[int(rng.integers(0, len(resolutions)))]
+        out.append(Request(i, tree, w, h, poses(rng, tree, w, h), t))
+    return out
+
+
+def percentiles(reqs: Sequence[Request]):
+    lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
+
+
+# ----------------------------------------------------------------------------------------------
+# device side
+# ----------------------------------------------------------------------------------------------
+class _Table:
+    def __init__(self, torch, max_slots):
+        nbytes = HEADER_BYTES + SLOT_BYTES * max_slots
+        self.host = torch.zeros(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.dev = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+        self.counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.stream = torch.cuda.Stream()
+        self.graph = None
+        self.event = torch.cuda.Event()
+        self.reqs: List[Request] = []
+
+
+class BatchedServer:
+    def __init__(self, trees, opts, pool_floats: int, max_slots: int = 256, n_tables: int = 2):
+        import torch
+
+        from . import dot
+        self.torch, self.dot = torch, dot
+        self.trees = list(trees)
+        self.handles = (ctypes.c_void_p * len(self.trees))(*[t.handle.value for t in self.trees])
+        self.opts = opts
+        self.max_slots = max_slots
+        self.pool_t = torch.empty(int(pool_floats), dtype=torch.float32, device="cuda")
+        self.pool = OutputPool(pool_floats)
+        self.tables = [_Table(torch, max_slots) for _ in range(n_tables)]
+        for tb in self.tables:
+            self._capture(tb)
+
+    def _launch(self, tb):
+        rc = self.dot.lib().dot_render_slots(self.handles, len(self.trees),
+                                             ctypes.c_void_p(tb.dev.data_ptr()), self.max_slots,
+                                             ctypes.byref(self.opts),
+                                             ctypes.c_void_p(tb.counter.data_ptr()),
+                                             ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            raise self.dot.DotError(rc, self.dot.dot_last_error())
+
+    def _capture(self, tb):
+        torch = self.torch
+        with torch.cuda.stream(tb.stream):          # one eager run before capture
+            tb.dev.copy_(tb.host, non_blocking=True)
+            self._launch(tb)
+        torch.cuda.synchronize()
+        tb.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(tb.graph, stream=tb.stream):
+            tb.dev.copy_(tb.host, non_blocking=True)
+            self._launch(tb)
+        torch.cuda.synchronize()
+
+    def submit(self, reqs: List[Request], tb: _Table):
+        img = pack_table(reqs, self.pool_t.data_ptr(), self.max_slots)
+        tb.host.numpy()[:] = img
+        tb.reqs = reqs
+        with self.torch.cuda.stream(tb.stream):
+            tb.graph.replay()
+            tb.event.record(tb.stream)
+
+    def run(self, trace: Sequence[Request], clock=time.perf_counter):
+        """Replays the trace in real time; fills r.done for every request."""
+        pending: deque = deque()
+        free_tables = list(self.tables)
+        busy: List[_Table] = []
+        i, n, finished = 0, len(trace), 0
+        t0 = clock()
+        while finished < n:
+            now = clock() - t0
+            while i < n and trace[i].arrival <= now:
+                pending.append(trace[i])
+                i += 1
+            for tb in list(busy):
+                if tb.event.query():
+                    t = clock() - t0
+                    for r in tb.reqs:
+                        r.done = t
+                        self.pool.release(r.offset, r.floats)
+                    finished += len(tb.reqs)
+                    busy.remove(tb)
+                    free_tables.append(tb)
+            if pending and free_tables:
+                batch = []
+                while pending and len(batch) < self.max_slots:
+                    r = pending[0]
+                    off = self.pool.alloc(r.floats)
+                    if off < 0:
+                        break                          # admitted later, as memory frees up
+                    r.offset = off
+                    batch.append(pending.popleft())
+                if batch:
+                    tb = free_tables.pop()
+                    self.submit(batch, tb)
+                    busy.append(tb)
+        return trace
+
+    def render_alone_and_mixed(self, reqs: List[Request]):
+        """Device images of `reqs` rendered all in one table, and each in a table of its own."""
+        torch = self.torch
+        tb = self.tables[0]
+        for r in reqs:
+            r.offset = self.pool.alloc(r.floats)
+            assert r.offset >= 0
+        self.submit(list(reqs), tb)
+        torch.cuda.synchronize()
+        mixed = [self.pool_t[r.offset: r.offset + r.floats].clone() for r in reqs]
+        alone = []
+        for r in reqs:
+            self.pool_t[r.offset: r.offset + r.floats].fill_(-1.0)
+            self.submit([r], tb)
+            torch.cuda.synchronize()
+            alone.append(self.pool_t[r.offset: r.offset + r.floats].clone())
+        for r in reqs:
+            self.pool.release(r.offset, r.floats)
+        return mixed, alone
+
+
+class PlainServer:
+    """One dot_render_forward launch per request, in arrival order, on one stream."""
+
+    def __init__(self, trees, opts, pool_floats: int):
+        import torch
+
+        from . import dot
+        self.torch, self.dot = torch, dot
+        self.trees = list(trees)
+        self.opts = opts
+        self.pool_t = torch.empty(int(pool_floats), dtype=torch.float32, device="cuda")
+        self.pool = OutputPool(pool_floats)
+        self.stream = torch.cuda.Stream()
+        self.cams = torch.zeros(18, dtype=torch.float32, pin_memory=True)
+
+    def run(self, trace: Sequence[Request], clock=time.perf_counter):
+        torch, dot = self.torch, self.dot
+        pending: deque = deque()
+        inflight: deque = deque()
+        i, n, finished = 0, len(trace), 0
+        t0 = clock()
+        while finished < n:
+            now = clock() - t0
+            while i < n and trace[i].arrival <= now:
+                pending.append(trace[i])
+                i += 1
+            while inflight and inflight[0][1].query():
+                r, ev, cam = inflight.popleft()
+                r.done = clock() - t0
+                self.pool.release(r.offset, r.floats)
+                finished += 1
+            while pending:
+                r = pending[0]
+                off = self.pool.alloc(r.floats)
+                if off < 0:
+                    break
+                pending.popleft()
+                r.offset = off
+                with torch.cuda.stream(self.stream):
+                    cam = torch.from_numpy(np.ascontiguousarray(r.camera)).to("cuda", non_blocking=False).view(1, 18)
+                    out = self.pool_t[off: off + r.floats]
+                    dot.dot_render_forward(self.trees[r.tree], dot.rays_cameras(cam, r.width, r.height),
+                                           self.opts, out, stream=self.stream)
+                    ev = torch.cuda.Event()
+                    ev.record(self.stream)
+                inflight.append((r, ev, cam))
+        return trace

@@ -452,3 +452,31 @@ def random_masks(n: int, seed: int, p_prune: float = 0.6, p_sample: float = 0.05
     prune = (rng.random(n) < p_prune).astype(np.uint8)
     sample = (rng.random(n) < p_sample).astype(np.uint8)
     return prune, sample
+
+
+# ----------------------------------------------------------------------------------------------
+# serving workload
+# ----------------------------------------------------------------------------------------------
+
+SERVE_RESOLUTIONS = [(256, 256), (512, 512), (800, 800), (1280, 720), (1920, 1080)]
+
+
+def config_serving():
+    """Four resident scenes for the serving loop -- the NeRF-synthetic-shaped scene, the
+    Tanks&Temples-shaped scene and two seed variants of the first -- all stored FP16 with SH
+    degree 3 (one slot launch serves one storage type), and a pose sampler: a random direction on
+    the upper hemisphere at the scene's viewing distance, focal scaled with the width as in the
+    scene's own config (1111 per 800 px, 1200 per 1920 px)."""
+    scenes = [nerf_synthetic_scene(seed=1000), tanks_temples_scene(seed=3000, storage=STORAGE_F16),
+              nerf_synthetic_scene(seed=1010), nerf_synthetic_scene(seed=1020)]
+    dist = [4.0, 5.0, 4.0, 4.0]
+    focal_per_px = [1111.0 / 800.0, 1200.0 / 1920.0, 1111.0 / 800.0, 1111.0 / 800.0]
+
+    def poses(rng, tree, w, h):
+        y = rng.uniform(0.05, 0.95)
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        r = math.sqrt(1.0 - y * y)
+        pos = dist[tree] * np.array([r * math.cos(phi), y, r * math.sin(phi)])
+        return pinhole(pos, w, h, focal_per_px[tree] * w).packed()
+
+    return scenes, poses
