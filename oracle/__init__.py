@@ -89,6 +89,10 @@ def lib():
                                         ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_Counts)]
+            L.oracle_mse.argtypes = [ctypes.c_int64, P, P, P]
+            L.oracle_mse.restype = ctypes.c_double
+            L.oracle_rmsprop.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double]
             L.oracle_free.argtypes = [P]
             _lib = L
     return _lib
@@ -275,6 +279,25 @@ def refine(tree, sigma, sh, prune_mark, sample_mark, d_cap):
         L.oracle_free(p)
     counts = {k: getattr(cnt, k) for k, _ in _Counts._fields_}
     return new, lm, so, sho, counts
+
+
+def mse(rgb, target):
+    """Loss and gradient of the MSE of Algorithm 1 (optimization) over rays x 3 channels."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64).reshape(-1, 3)
+    target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 3)
+    grad = np.zeros_like(rgb)
+    loss = lib().oracle_mse(rgb.shape[0], _ptr(rgb), _ptr(target), _ptr(grad))
+    return loss, grad
+
+
+def rmsprop(param, ms, grad, lr, rho, eps):
+    """One RMSProp step (Sec. 3.3) on copies: returns (param_new, ms_new), float64."""
+    p = np.array(param, dtype=np.float64, copy=True, order="C")
+    m = np.array(ms, dtype=np.float64, copy=True, order="C")
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    assert p.size == m.size == g.size
+    lib().oracle_rmsprop(p.size, _ptr(p), _ptr(m), _ptr(g), float(lr), float(rho), float(eps))
+    return p, m
 
 
 def key_level(keys) -> np.ndarray:

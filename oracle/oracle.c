@@ -616,3 +616,32 @@ int oracle_refine(const otree *t, const double *sigma, const double *sh, int32_t
     free(inner_new); free(child_base);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* optimisation step (Algorithm 1, optimization; Sec. 3.3; Sec. 4.1)                           */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Mean squared error of the prediction against the target over n rays x 3 channels (Algorithm 1
+ * computes loss = MSE(pred, GT) on stochastic image samples, Sec. 4.1):
+ * loss = (1 / 3n) sum (rgb - target)^2, and its gradient 2 (rgb - target) / 3n. */
+double oracle_mse(int64_t n, const double *rgb, const double *target, double *grad) {
+    double loss = 0.0;
+    const double inv = n > 0 ? 1.0 / (3.0 * (double)n) : 0.0;
+    for (int64_t i = 0; i < 3 * n; i++) {
+        const double e = rgb[i] - target[i];
+        loss += e * e;
+        if (grad) grad[i] = 2.0 * e * inv;
+    }
+    return loss * inv;
+}
+
+/* One RMSProp update of n parameters (Sec. 3.3 optimises the cached coefficients with RMSProp;
+ * Sec. 4.1 gives learning rates 0.1 for sigma and 0.01 for the SH colour):
+ *   ms <- rho ms + (1 - rho) g^2,   p <- p - lr g / (sqrt(ms) + eps). */
+void oracle_rmsprop(int64_t n, double *param, double *ms, const double *grad, double lr,
+                    double rho, double eps) {
+    for (int64_t i = 0; i < n; i++) {
+        ms[i] = rho * ms[i] + (1.0 - rho) * grad[i] * grad[i];
+        param[i] = param[i] - lr * grad[i] / (sqrt(ms[i]) + eps);
+    }
+}

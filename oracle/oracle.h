@@ -76,6 +76,15 @@ int oracle_refine(const otree *t, const double *sigma, const double *sh, int32_t
                   otree *out, int32_t **leaf_map, double **sigma_out, double **sh_out,
                   orefine_counts *counts);
 
+/* MSE over n rays x 3 channels (Algorithm 1, optimization): returns (1/3n) sum (rgb - target)^2
+ * and writes its gradient 2 (rgb - target) / 3n to grad (nullable). */
+double oracle_mse(int64_t n, const double *rgb, const double *target, double *grad);
+
+/* RMSProp (Sec. 3.3) in place over n entries: ms <- rho ms + (1 - rho) g^2,
+ * p <- p - lr g / (sqrt(ms) + eps). */
+void oracle_rmsprop(int64_t n, double *param, double *ms, const double *grad, double lr,
+                    double rho, double eps);
+
 void oracle_free(void *p);
 
 #endif
