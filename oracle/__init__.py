@@ -93,6 +93,8 @@ def lib():
             L.oracle_mse.restype = ctypes.c_double
             L.oracle_rmsprop.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double]
+            L.oracle_median_cut.argtypes = [ctypes.c_int64, ctypes.c_int32, P, ctypes.c_int32,
+                                            P, P]
             L.oracle_free.argtypes = [P]
             _lib = L
     return _lib
@@ -298,6 +300,61 @@ def rmsprop(param, ms, grad, lr, rho, eps):
     assert p.size == m.size == g.size
     lib().oracle_rmsprop(p.size, _ptr(p), _ptr(m), _ptr(g), float(lr), float(rho), float(eps))
     return p, m
+
+
+def remap_leaf_values(old_tree, leaf_map, values, merge="mean"):
+    """Per-leaf values carried through a refine: a surviving or copied leaf takes its source
+    leaf's value; a merged parent (leaf_map = -1 - p) the mean, sum or max of its 8 children's
+    (Eq. 3 for the mean).  values [L_old, ...] float64 -> [L_new, ...]."""
+    v = np.asarray(values, dtype=np.float64)
+    out = np.empty((len(leaf_map),) + v.shape[1:], np.float64)
+    child = old_tree["child"]
+    for u, m in enumerate(leaf_map):
+        if m >= 0:
+            out[u] = v[m]
+            continue
+        kids = v[[-1 - c for c in child[-1 - m]]]
+        if merge == "max":
+            out[u] = kids.max(axis=0)
+        elif merge == "sum":
+            out[u] = kids.sum(axis=0)
+        else:
+            out[u] = kids.mean(axis=0)
+    return out
+
+
+def prune_recursive(tree, sigma, sh, signal, tau, d_cap, recursive=True, merge="sum", aux=()):
+    """Algorithm 1's pruning: merge every group whose 8 leaves all have signal <= tau (Sec. 3.2
+    threshold), and, when recursive, repeat on the merged tree -- a merged parent's signal being
+    the sum (or max) of its children's -- until no group qualifies.  aux: per-leaf arrays carried
+    along as means.  Returns (tree, sigma, sh, signal, aux, passes)."""
+    aux = [np.asarray(a, np.float64) for a in aux]
+    passes = []
+    while True:
+        pm, _ = select(signal, SELECT_THRESHOLD, tau)
+        sm = np.zeros_like(pm)
+        new, lm, so, sho, cnt = refine(tree, sigma, sh, pm, sm, d_cap)
+        if cnt["n_pruned_groups"] == 0:
+            break
+        signal = remap_leaf_values(tree, lm, signal, merge)
+        aux = [remap_leaf_values(tree, lm, a, "mean") for a in aux]
+        tree, sigma, sh = new, so, sho
+        passes.append(cnt)
+        if not recursive:
+            break
+    return tree, sigma, sh, signal, aux, passes
+
+
+def median_cut(x, bits):
+    """Median-cut quantisation (Sec. 4.1, compressed models) of the rows of x [n, dim] into
+    2^bits boxes: returns (index [n] int32, palette [2^bits, dim] float64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, dim = x.shape
+    index = np.zeros(n, np.int32)
+    pal = np.zeros((1 << bits, dim), np.float64)
+    rc = lib().oracle_median_cut(n, dim, _ptr(x), int(bits), _ptr(index), _ptr(pal))
+    assert rc == 0
+    return index, pal
 
 
 def key_level(keys) -> np.ndarray:

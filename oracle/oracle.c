@@ -645,3 +645,84 @@ void oracle_rmsprop(int64_t n, double *param, double *ms, const double *grad, do
         param[i] = param[i] - lr * grad[i] / (sqrt(ms[i]) + eps);
     }
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* compressed models: median-cut quantisation of the SH coefficient vectors (Sec. 4.1)          */
+/* ------------------------------------------------------------------------------------------ */
+
+static const double *mc_x;   /* the vectors being sorted (qsort has no context argument) */
+static int mc_dim, mc_axis;
+
+static int mc_cmp(const void *a, const void *b) {
+    const int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    const double u = mc_x[i * mc_dim + mc_axis], v = mc_x[j * mc_dim + mc_axis];
+    if (u < v) return -1;
+    if (u > v) return 1;
+    return (i > j) - (i < j);
+}
+
+/* Median cut (Heckbert 1982, the quantiser Sec. 4.1 applies to the SH coefficients): n vectors of
+ * dimension dim go into 2^bits boxes.  Starting from one box holding every vector, each of the
+ * bits rounds splits every box of two or more vectors at the median of its longest side: the
+ * axis of largest (max - min) (ties to the lowest axis), members ordered by (value on that axis,
+ * vector id), the first floor(m/2) to child 2b and the rest to child 2b+1 (a box of fewer than two
+ * keeps its members in child 2b).  The palette entry of a box is the mean of its members (zeros
+ * for an empty box).  index[n] receives each vector's box; palette is [2^bits][dim]. */
+int oracle_median_cut(int64_t n, int32_t dim, const double *x, int32_t bits, int32_t *index,
+                      double *palette) {
+    const int64_t P = (int64_t)1 << bits;
+    int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *start = (int64_t *)calloc((size_t)P + 1, sizeof(int64_t));
+    int64_t *nstart = (int64_t *)calloc((size_t)P + 1, sizeof(int64_t));
+    if (!order || !start || !nstart) return -1;
+    for (int64_t i = 0; i < n; i++) order[i] = i;
+    int64_t boxes = 1;
+    start[0] = 0;
+    start[1] = n;
+    mc_x = x;
+    mc_dim = dim;
+    for (int r = 0; r < bits; r++) {
+        for (int64_t b = 0; b < boxes; b++) {
+            const int64_t s = start[b], e = start[b + 1], m = e - s;
+            nstart[2 * b] = s;
+            if (m < 2) {
+                nstart[2 * b + 1] = e;
+                continue;
+            }
+            int axis = 0;
+            double best = -1.0;
+            for (int d = 0; d < dim; d++) {
+                double lo = x[order[s] * dim + d], hi = lo;
+                for (int64_t k = s + 1; k < e; k++) {
+                    const double v = x[order[k] * dim + d];
+                    if (v < lo) lo = v;
+                    if (v > hi) hi = v;
+                }
+                if (hi - lo > best) {
+                    best = hi - lo;
+                    axis = d;
+                }
+            }
+            mc_axis = axis;
+            qsort(order + s, (size_t)m, sizeof(int64_t), mc_cmp);
+            nstart[2 * b + 1] = s + m / 2;
+        }
+        nstart[2 * boxes] = n;
+        boxes *= 2;
+        for (int64_t b = 0; b <= boxes; b++) start[b] = nstart[b];
+    }
+    for (int64_t b = 0; b < P; b++) {
+        for (int d = 0; d < dim; d++) palette[b * dim + d] = 0.0;
+        const int64_t s = start[b], e = start[b + 1];
+        for (int64_t k = s; k < e; k++) {
+            index[order[k]] = (int32_t)b;
+            for (int d = 0; d < dim; d++) palette[b * dim + d] += x[order[k] * dim + d];
+        }
+        if (e > s)
+            for (int d = 0; d < dim; d++) palette[b * dim + d] /= (double)(e - s);
+    }
+    free(order);
+    free(start);
+    free(nstart);
+    return 0;
+}

@@ -85,6 +85,13 @@ double oracle_mse(int64_t n, const double *rgb, const double *target, double *gr
 void oracle_rmsprop(int64_t n, double *param, double *ms, const double *grad, double lr,
                     double rho, double eps);
 
+/* Median cut (Heckbert 1982; Sec. 4.1 compressed models) of n vectors of dimension dim into
+ * 2^bits boxes, every round splitting every box of >= 2 members at the median of its longest
+ * axis (ties: lowest axis; order (value, id); floor(m/2) members to the lower child).  Writes each
+ * vector's box to index[n] and the box means (zeros when empty) to palette[2^bits][dim]. */
+int oracle_median_cut(int64_t n, int32_t dim, const double *x, int32_t bits, int32_t *index,
+                      double *palette);
+
 void oracle_free(void *p);
 
 #endif

@@ -179,3 +179,67 @@ def test_select_threshold_and_rank():
         e = np.zeros(s.size, np.uint8)
         e[bot] = 1
         np.testing.assert_array_equal(pm, e)
+
+
+# ----------------------------------------------------------------------------------------------
+# recursive pruning (Sec. 3.2, Algorithm 1 with rec)
+# ----------------------------------------------------------------------------------------------
+def _full_depth3():
+    """Every cell of a depth-3 tree meets the box [0, 1]^3 -> 1 + 8 + 64 nodes, 512 leaves."""
+    prims = np.array([[si.PRIM_BOX, 0, 0, 0, Q, Q, Q, 0]], np.int64)
+    t = oracle.build_tree(prims, 3)
+    assert t["leaf_key"].size == 512 and t["node_key"].size == 73
+    return t
+
+
+def test_recursive_prune_of_a_silent_tree_collapses_to_the_root():
+    t = _full_depth3()
+    rng = np.random.default_rng(0)
+    sigma = rng.uniform(1, 2, 512)
+    sh = rng.normal(size=(512, 3, 1))
+    sig = np.zeros(512, np.float32)
+    nt, so, sho, s2, _, passes = oracle.prune_recursive(t, sigma, sh, sig, 0.0, d_cap=8)
+    assert [p["n_pruned_groups"] for p in passes] == [64, 8]
+    assert nt["leaf_key"].size == 8 and nt["node_key"].size == 1
+    # each level-1 leaf holds the mean of the 64 finest leaves below it (Eq. 3 applied twice)
+    keys = t["leaf_key"]
+    for u, k in enumerate(nt["leaf_key"]):
+        below = (keys >> np.uint64(6)) == k
+        assert below.sum() == 64
+        assert so[u] == pytest.approx(sigma[below].mean(), rel=1e-14)
+        np.testing.assert_allclose(sho[u], sh[below].mean(axis=0), rtol=1e-13, atol=1e-15)
+    one = oracle.prune_recursive(t, sigma, sh, sig, 0.0, d_cap=8, recursive=False)
+    assert [p["n_pruned_groups"] for p in one[5]] == [64] and one[0]["leaf_key"].size == 64
+
+
+@pytest.mark.parametrize("merge,expect_passes,n_leaves",
+                         [("sum", [511, 63], 63 + 7 + 8), ("max", [511, 63, 7], 7 + 7 + 7 + 8)])
+def test_recursive_prune_merged_signal(merge, expect_passes, n_leaves):
+    """Full depth-4 tree; one loud leaf (1.0) blocks its group, quiet leaves carry 0.01, tau = 0.5.
+    Each pass thresholds the current leaves: merged parents carry 0.08 then 0.64 with sum (the
+    third pass finds 0.64 > tau and stops) or stay at 0.01 with max (the third pass merges the 7
+    level-1 cells whose children are all leaves)."""
+    prims = np.array([[si.PRIM_BOX, 0, 0, 0, Q, Q, Q, 0]], np.int64)
+    t = oracle.build_tree(prims, 4)
+    assert t["leaf_key"].size == 4096
+    sigma = np.ones(4096)
+    sh = np.zeros((4096, 3, 1))
+    sig = np.full(4096, 0.01, np.float32)
+    sig[1234] = 1.0
+    nt, _, _, s2, _, passes = oracle.prune_recursive(t, sigma, sh, sig, 0.5, d_cap=8, merge=merge)
+    assert [p["n_pruned_groups"] for p in passes] == expect_passes
+    assert nt["leaf_key"].size == n_leaves
+    assert s2.max() == pytest.approx(1.0)
+    assert np.isin(t["leaf_key"][1234], nt["leaf_key"])
+    if merge == "sum":
+        assert np.sort(s2)[-2] == pytest.approx(0.64, rel=1e-6)
+
+
+def test_remap_leaf_values_by_hand():
+    t = _depth1_tree()
+    nt, lm, _, _, _ = oracle.refine(t, np.ones(8), np.zeros((8, 3, 1)), np.ones(8, np.uint8),
+                                    np.zeros(8, np.uint8), d_cap=8)
+    # the root is never merged: nothing changes
+    assert lm.tolist() == list(range(8))
+    s = np.arange(8, dtype=np.float64)
+    np.testing.assert_array_equal(oracle.remap_leaf_values(t, lm, s), s)
