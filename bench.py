@@ -44,6 +44,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true",
+                   help="skip the training-loop and Tanks&Temples-shaped measurements")
     p.add_argument("--serve-requests", type=int, default=1000,
                    help="requests per serving trace at 200 req/s (twice as many at 2000 req/s)")
     return p.parse_args()
@@ -214,6 +216,131 @@ def measure_serving(args):
     return res
 
 
+def alg_bytes_of(stats, n_rays, storage_bytes, K):
+    """Algorithmic bytes of one forward launch: the leaf payload of every occupied segment
+    (density + SH row), the density of every other segment, one child word per segment, and the
+    12-byte colour of every ray."""
+    P = (1 + 3 * K) * storage_bytes
+    seg, occ = stats["segments"], stats["occupied"]
+    return occ * P + (seg - occ) * storage_bytes + seg * 4 + n_rays * 12
+
+
+def timed(fn, n, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_training(scene, cams, steps: int):
+    """Algorithm 1 on the NeRF-synthetic-shaped scene: optimisation steps on 2^16-ray batches
+    (forward with the fused SUM_ALPHA signal, MSE gradient, backward, RMSProp of every leaf fused
+    with zeroing the gradients) against targets rendered from a seeded perturbed copy of the tree
+    (same cells, other seed), then one refine (recursive pruning at the 20th-percentile signal,
+    sampling of the top 5%)."""
+    import dataclasses
+
+    import torch
+
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.train import Trainer
+    stream = torch.cuda.current_stream()
+    tree = dot.octree_from_scene(scene)
+    ref = dot.octree_from_scene(dataclasses.replace(scene, seed=scene.seed + 1))
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    nb = 8
+    batches, targets = [], []
+    for i in range(nb):
+        o, d = si.ray_batch(cams, BATCH, seed=9000 + i)
+        r = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+        t = torch.empty(BATCH, 3, device="cuda")
+        dot.dot_render_forward(ref, r, opts, t)
+        batches.append(r)
+        targets.append(t)
+    ref.free()
+    tr = Trainer(tree, opts, dot.dot.rmsprop_opts(), signal_mode=dot.dot.DOT_SIGNAL_SUM_ALPHA)
+    for i in range(5):
+        tr.step(batches[i % nb], targets[i % nb])
+    torch.cuda.synchronize()
+    tr.loss_sum.zero_()
+    n = max(50, steps)
+    ms = timed(lambda i: tr.step(batches[i % nb], targets[i % nb]), n, stream)
+    loss = float(tr.loss_sum) / n
+    L0 = tr.L
+    q = float(torch.quantile(tr.signal[tr.signal > 0].float()[:1 << 24], 0.2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = tr.refine(q, 0.05, depth_cap=11, recursive=True)
+    torch.cuda.synchronize()
+    refine_ms = (time.perf_counter() - t0) * 1e3
+    out = {"value": BATCH * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "iters_per_s": n / (ms / 1e3),
+           "ms_per_iter": ms / n, "batch_rays": BATCH, "iters": n, "mean_batch_mse": loss,
+           "leaves": L0, "step": "fwd+signal, mse grad, bwd, rmsprop(all leaves)+zero grad",
+           "refine": {"ms": refine_ms, "tau": q, "gamma": 0.05, "recursive": True,
+                      "pruned_groups_per_pass": [p["n_pruned_groups"] for p in res["passes"]],
+                      "leaves_after": res["n_leaves"]}}
+    tree.free()
+    return out
+
+
+def measure_tanks_temples(steps: int):
+    """Forward (all 150 views of 1920x1080 in one launch, 311 M rays) and forward+backward
+    (2^16-ray batches) on the Tanks&Temples-shaped scene (depth 10, BF16 leaves, SH degree 3)."""
+    import torch
+
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    stream = torch.cuda.current_stream()
+    scene, cams = si.config_tanks_temples()
+    tree = dot.octree_from_scene(scene)
+    W, H = cams[0].width, cams[0].height
+    cam_t = dot.cameras_tensor(cams)
+    rays = dot.rays_cameras(cam_t, W, H)
+    R = len(cams) * W * H
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    rgb = torch.empty(R, 3, device="cuda")
+    st = dot.dot_render_stats(tree, rays, opts)
+    ab = alg_bytes_of(st, R, 2, scene.n_coeffs)
+    dot.dot_render_forward(tree, rays, opts, rgb)
+    torch.cuda.synchronize()
+    n = max(3, min(steps, 10))
+    ms = timed(lambda i: dot.dot_render_forward(tree, rays, opts, rgb), n, stream)
+    hbm, kind = peaks()
+    L, K = tree.n_leaves, scene.n_coeffs
+    batches = []
+    for i in range(8):
+        o, d = si.ray_batch(cams, BATCH, seed=11000 + i)
+        batches.append(dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()))
+    g = torch.full((BATCH, 3), 1e-3, device="cuda")
+    brgb = torch.empty(BATCH, 3, device="cuda")
+    gs = torch.zeros(L, device="cuda")
+    gsh = torch.zeros(L, 3, K, device="cuda")
+
+    def pair(i):
+        r = batches[i % 8]
+        dot.dot_render_forward(tree, r, opts, brgb)
+        dot.dot_render_backward(tree, r, opts, g, brgb, gs, gsh)
+    for i in range(8):
+        pair(i)
+    torch.cuda.synchronize()
+    pms = timed(pair, 100, stream)
+    out = {"workload": "tanks_temples_d10_sh3_bf16_150x1920x1080", "leaves": L,
+           "nodes": tree.n_nodes, "rays_per_step": R,
+           "fwd": {"value": R * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms / n,
+                   "roofline_frac": ab / (ms / n / 1e3) / 1e9 / hbm, "peak_kind": kind,
+                   "alg_bytes_per_launch": ab, "segments_per_ray": st["segments"] / R,
+                   "occupied_per_ray": st["occupied"] / R},
+           "fwd_bwd": {"value": BATCH * 100 / (pms / 1e3) / 1e6, "unit": "Mrays/s",
+                       "batch_rays": BATCH, "ms_per_pair": pms / 100}}
+    tree.free()
+    return out
+
+
 # ----------------------------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ----------------------------------------------------------------------------------------------
@@ -287,7 +414,7 @@ def run_dot(args):
     K = scene.n_coeffs
     P = (1 + 3 * K) * bs                                  # leaf payload of an occupied segment
     seg, occ = st["segments"], st["occupied"]
-    alg_bytes = occ * P + (seg - occ) * bs + seg * 4 + R * 12
+    alg_bytes = alg_bytes_of(st, R, bs, K)
 
     # ---- forward: W warm-up steps, K timed steps, one launch each ----
     for _ in range(args.warmup):
@@ -400,6 +527,8 @@ def run_dot(args):
               "signal": f"MAX_WEIGHT over {nb} x 2^16 rays", "select": "bottom 20% / top 5%"}
 
     serve_res = measure_serving(args) if rank == 0 else None
+    train_res = measure_training(scene, cams, args.steps) if rank == 0 and not args.quick else None
+    tt_res = measure_tanks_temples(args.steps) if rank == 0 and not args.quick else None
 
     hbm, peak_kind = peaks()
     achieved = alg_bytes / mean_launch_s / 1e9
@@ -427,7 +556,8 @@ def run_dot(args):
                              "vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6),
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "serve": serve_res,
+            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "train": train_res,
+            "tanks_temples": tt_res, "serve": serve_res,
             "wall_s_timed": t_wall}
     if rank == 0:
         print(json.dumps(line))

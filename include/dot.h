@@ -359,6 +359,38 @@ int dot_refine_prune(dot_tree *tree, const uint8_t *prune_mark, const uint8_t *s
                      int32_t depth_cap, int32_t *leaf_map, const dot_leaf_array *aux,
                      int32_t n_aux, void *stream);
 
+/* RMSProp hyper-parameters (Sec. 3.3 names RMSProp; Sec. 4.1 gives lr 0.1 for sigma and 0.01
+ * for the SH colour; the decay rho and eps are not given: the usual 0.9 and 1e-8 are defaults of
+ * the Python binding). */
+typedef struct {
+    float lr_sigma, lr_sh;
+    float rho;          /* decay of the mean square, in [0, 1) */
+    float eps;          /* added to sqrt(mean square), >= 0 */
+    int32_t zero_grad;  /* 1: write zeros to the gradients after reading them */
+} dot_rmsprop_opts;
+
+/*
+ * dot_mse_grad -- the MSE loss of Algorithm 1 (optimization) over R rays x 3 channels of
+ * stochastic samples (Sec. 4.1): grad_rgb = 2 (rgb - target) / (3R), the input of
+ * dot_render_backward, and loss_sum += sum (rgb - target)^2 / (3R).
+ * rgb, target, grad_rgb: device [R][3] float (grad_rgb may alias neither input); loss_sum: device
+ * double (accumulated; may be NULL).  R = 0 is a no-op.
+ */
+int dot_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad_rgb,
+                 double *loss_sum, void *stream);
+
+/*
+ * dot_rmsprop_step -- one RMSProp update of every leaf's density and SH coefficients in place
+ * (Sec. 3.3), FP32 arithmetic, parameters rounded to the storage type:
+ *   ms <- rho ms + (1 - rho) g^2,   p <- p - lr g / (sqrt(ms) + eps)
+ * with lr = lr_sigma for sigma and lr_sh for the SH coefficients; with zero_grad the gradients are
+ * zeroed in the same pass (ready for the next dot_render_backward).
+ * grad_sigma, ms_sigma: device [L] float; grad_sh, ms_sh: device [L][3][K] float.  The tree's
+ * parameters change; its structure does not.
+ */
+int dot_rmsprop_step(dot_tree *tree, float *grad_sigma, float *grad_sh, float *ms_sigma,
+                     float *ms_sh, const dot_rmsprop_opts *opts, void *stream);
+
 /*
  * dot_render_stats -- counts of the march for these rays (not part of any hot path): out[0] =
  * rays entering the root, out[1] = segments (cell steps), out[2] = occupied segments

@@ -28,6 +28,11 @@ cudaError_t launch_march_signal(int storage, bool exact, const TreeView &tv, con
                                 const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
 cudaError_t launch_march_stats(int storage, bool exact, const TreeView &tv, const RaySource &rs,
                                const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
+cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad,
+                            double *loss_sum, cudaStream_t s);
+cudaError_t launch_rmsprop(int storage, void *sigma, void *sh, int64_t L, int K, int row_stride,
+                           float *grad_sigma, float *grad_sh, float *ms_sigma, float *ms_sh,
+                           const dot_rmsprop_opts &op, cudaStream_t s);
 }  // namespace dot
 
 namespace {
@@ -623,5 +628,34 @@ extern "C" int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const v
                                     n_trees, table, max_slots, rp, work_counter, trees[0]->status,
                                     0, S(stream)),
            "dot_render_slots");
+    return DOT_OK;
+}
+
+extern "C" int dot_mse_grad(const float *rgb, const float *target, int64_t n_rays,
+                            float *grad_rgb, double *loss_sum, void *stream) {
+    if (n_rays < 0) return fail(DOT_ERR_INVALID_ARG, "n_rays < 0");
+    if (n_rays == 0) return DOT_OK;
+    if (!rgb || !target || !grad_rgb) return fail(DOT_ERR_INVALID_ARG, "rgb, target and grad_rgb are required");
+    if (grad_rgb == rgb || grad_rgb == target)
+        return fail(DOT_ERR_INVALID_ARG, "grad_rgb must not alias rgb or target");
+    API_CK(dot::launch_mse_grad(rgb, target, n_rays, grad_rgb, loss_sum, S(stream)), "dot_mse_grad");
+    return DOT_OK;
+}
+
+extern "C" int dot_rmsprop_step(dot_tree *t, float *grad_sigma, float *grad_sh, float *ms_sigma,
+                                float *ms_sh, const dot_rmsprop_opts *opts, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    if (t->a.n_leaves == 0) return DOT_OK;
+    if (!grad_sigma || !grad_sh || !ms_sigma || !ms_sh)
+        return fail(DOT_ERR_INVALID_ARG, "gradients and mean-square arrays are required");
+    if (!(opts->rho >= 0.f && opts->rho < 1.f)) return fail(DOT_ERR_INVALID_ARG, "rho must be in [0, 1)");
+    if (!(opts->eps >= 0.f) || !std::isfinite(opts->lr_sigma) || !std::isfinite(opts->lr_sh))
+        return fail(DOT_ERR_INVALID_ARG, "eps must be >= 0 and learning rates finite");
+    API_CK(dot::launch_rmsprop(t->a.storage, t->a.sigma, t->a.sh, t->a.n_leaves, t->a.K,
+                               t->a.row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh, *opts,
+                               S(stream)),
+           "dot_rmsprop_step");
     return DOT_OK;
 }

@@ -18,7 +18,6 @@
 
 #include <type_traits>
 
-
 #include "internal.cuh"
 
 namespace dot {
@@ -97,6 +96,15 @@ __device__ __forceinline__ void leaf_z(const S *row, const float *Y, float z[3])
     }
 }
 
+// requests the 16-byte-aligned SH row into L1 ahead of its use (both ends: a row may straddle
+// two 128-byte lines)
+template <typename S, int K>
+__device__ __forceinline__ void prefetch_row(const S *row) {
+    const char *b = reinterpret_cast<const char *>(row);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b + Row<S, K>::kBytes - 1));
+}
+
 template <bool EXACT> __device__ __forceinline__ float ex(float x) {
     if constexpr (EXACT) return expf(x);
     else return __expf(x);
@@ -173,7 +181,11 @@ struct RayOut {
     unsigned long long st[4];  // STATS: hit, steps, occupied, child loads
 };
 
-template <typename S, int K, int MODE, bool EXACT>
+// NT: threads of the block (stride of the shared path stack).  DEFER: shade each occupied
+// segment one occupied segment later, after prefetching its SH row into L1, so that the row's
+// latency overlaps the traversal in between (a gain for launches too small to hide latency by
+// occupancy).
+template <typename S, int K, int MODE, bool EXACT, int NT = kMarchThreads, bool DEFER = false>
 __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams &rp,
                                           const RenderIO &io, int64_t ray, const float ow[3],
                                           const float dw[3], int32_t *stack, RayOut &out) {
@@ -253,7 +265,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         while (true) {
             const int sh = kGridBits - 1 - level;
             const int j = (((gc[0] >> sh) & 1) << 2) | (((gc[1] >> sh) & 1) << 1) | ((gc[2] >> sh) & 1);
-            stack[level * kMarchThreads] = node;
+            stack[level * NT] = node;
             c = __ldg(tv.child + (int64_t)node * 8 + j);
             ++level;
             if constexpr (MODE == kStats) out.st[3] += 1;
@@ -264,6 +276,56 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         level_out = level;
         return c < 0;  // false: deeper than the tree claims (corrupted table)
     };
+
+    // colour of one occupied segment (weight w, transmittance after it Tn, length delta):
+    // C += w c; the backward also scatters dL/dsigma and dL/dSH for it.  Segments are shaded in
+    // march order, so C is the prefix sum C_{<=i} the backward needs.
+    auto shade = [&](int32_t lf, float w, float Tn, float delta) {
+        if constexpr (MODE == kFwd || MODE == kBwd) {
+            float z[3], col[3];
+            leaf_z<S, K>(shp + (int64_t)lf * tv.row_stride, Y, z);
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++)
+                col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
+            if constexpr (MODE == kBwd) {
+                float acc = 0.f;
+                float dz[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) {
+                    const float suffix = rgbf[ch] - C[ch];
+                    acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
+                    const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
+                    dz[ch] = g[ch] * w * ag;
+                }
+                atomicAdd(io.grad_sigma + lf, delta * acc);
+                float *gr = io.grad_sh + (int64_t)lf * (3 * K);
+                if constexpr ((3 * K) % 4 == 0) {
+                    if (io.grad_vec) {
+                        float4 *g4 = reinterpret_cast<float4 *>(gr);
+#pragma unroll
+                        for (int q = 0; q < 3 * K / 4; q++) {
+                            float4 v;
+                            v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
+                            v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
+                            v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
+                            v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
+                            atomicAdd(g4 + q, v);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+                }
+            }
+        }
+    };
+    int32_t p_leaf = -1;  // deferred occupied segment (DEFER)
+    float p_w = 0.f, p_Tn = 0.f, p_delta = 0.f;
 
     PT t = tn;
     int32_t leaf;
@@ -320,13 +382,13 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (!outside) {
             const unsigned dbits = (unsigned)((gc[0] ^ lo_g[0]) | (gc[1] ^ lo_g[1]) | (gc[2] ^ lo_g[2]));
             const int lca = kGridBits - 1 - (31 - __clz(dbits));
-            if (!descend(stack[lca * kMarchThreads], lca, next_leaf, next_level)) {
+            if (!descend(stack[lca * NT], lca, next_leaf, next_level)) {
                 atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
                 next_level = -1;
             }
         }
 
-        // ---- shade the current segment ----
+        // ---- the current segment: density now, colour now or one occupied segment later ----
         if constexpr (MODE == kStats) out.st[1] += 1;
         bool stop = false;
         if (delta > 0.f && sv > 0.f) {
@@ -335,46 +397,15 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             const float alpha = 1.f - e;
             const float w = T * alpha;
             if constexpr (MODE == kFwd || MODE == kBwd) {
-                float z[3], col[3];
-                leaf_z<S, K>(shp + (int64_t)leaf * tv.row_stride, Y, z);
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++)
-                    col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
-                if constexpr (MODE == kBwd) {
-                    const float Tn = T * e;
-                    float acc = 0.f;
-                    float dz[3];
-#pragma unroll
-                    for (int ch = 0; ch < 3; ch++) {
-                        const float suffix = rgbf[ch] - C[ch];
-                        acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
-                        const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
-                        dz[ch] = g[ch] * w * ag;
-                    }
-                    atomicAdd(io.grad_sigma + leaf, delta * acc);
-                    float *gr = io.grad_sh + (int64_t)leaf * (3 * K);
-                    if constexpr ((3 * K) % 4 == 0) {
-                        if (io.grad_vec) {
-                            float4 *g4 = reinterpret_cast<float4 *>(gr);
-#pragma unroll
-                            for (int q = 0; q < 3 * K / 4; q++) {
-                                float4 v;
-                                v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
-                                v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
-                                v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
-                                v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
-                                atomicAdd(g4 + q, v);
-                            }
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                    }
+                if constexpr (DEFER) {
+                    prefetch_row<S, K>(shp + (int64_t)leaf * tv.row_stride);
+                    if (p_leaf >= 0) shade(p_leaf, p_w, p_Tn, p_delta);
+                    p_leaf = leaf;
+                    p_w = w;
+                    p_Tn = T * e;
+                    p_delta = delta;
+                } else {
+                    shade(leaf, w, T * e, delta);
                 }
             }
             if (MODE != kStats && io.signal != nullptr) {
@@ -389,6 +420,9 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (lt(t, tout)) t = tout;
         leaf = next_leaf;
         level = next_level;
+    }
+    if constexpr (DEFER && (MODE == kFwd || MODE == kBwd)) {
+        if (p_leaf >= 0) shade(p_leaf, p_w, p_Tn, p_delta);
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) out.rgb[ch] = fmaf(T, rp.bg[ch], C[ch]);
@@ -414,28 +448,38 @@ __device__ __forceinline__ void camera_ray(const dot_camera *cam, int i, int j, 
     for (int a = 0; a < 3; a++) d[a] = __fmul_rn(e[a], inv);
 }
 
-// MINB: minimum resident blocks per SM requested from the register allocator.  Launches large
-// enough to fill the GPU several times over run the MINB = 4 build (at most 64 registers, 32
-// warps per SM); small launches, whose time is the longest ray's latency, run MINB = 1.
-template <typename S, int K, int MODE, bool EXACT, int MINB>
-__global__ void __launch_bounds__(kMarchThreads, MINB)
+// Tile of pixels covered by a block of NT threads in camera mode: warps of 8x4 pixels, two
+// warps side by side when there are several (8 warps: 16x16, 4: 16x8, 2: 16x4, 1: 8x4).
+template <int NT> struct CamTile {
+    static constexpr int kWarps = NT / 32;
+    static constexpr int kW = kWarps >= 2 ? 16 : 8;
+    static constexpr int kH = kWarps >= 2 ? 4 * (kWarps / 2) : 4;
+};
+
+// MINB: minimum resident blocks per SM requested from the register allocator (MINB x NT = 1024
+// threads: at most 64 registers, 32 warps per SM, for launches large enough to fill the GPU
+// several times over; a single block's worth for small launches, whose time is the longest
+// ray's latency).
+template <typename S, int K, int MODE, bool EXACT, int MINB, int NT = kMarchThreads, bool DEFER = false>
+__global__ void __launch_bounds__(NT, MINB)
 march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
-    __shared__ int32_t s_stack[kMaxLevels * kMarchThreads];
+    __shared__ int32_t s_stack[kMaxLevels * NT];
     int32_t *stack = s_stack + threadIdx.x;
 
     int64_t ray;
     bool valid;
     float ow[3], dw[3];
     if (rs.kind == DOT_RAYS_CAMERAS) {
+        using TL = CamTile<NT>;
         const int tx = blockIdx.x % rs.tiles_x, ty = blockIdx.x / rs.tiles_x;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int px = tx * 16 + (warp & 1) * 8 + (lane & 7);
-        const int py = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+        const int px = tx * TL::kW + (warp % (TL::kW / 8)) * 8 + (lane & 7);
+        const int py = ty * TL::kH + (warp / (TL::kW / 8)) * 4 + (lane >> 3);
         valid = px < rs.width && py < rs.height;
         ray = ((int64_t)blockIdx.y * rs.height + py) * rs.width + px;
         if (valid) camera_ray(rs.cams + blockIdx.y, px, py, ow, dw);
     } else {
-        ray = (int64_t)blockIdx.x * kMarchThreads + threadIdx.x;
+        ray = (int64_t)blockIdx.x * NT + threadIdx.x;
         valid = ray < rs.n_rays;
         if (valid) {
 #pragma unroll
@@ -448,7 +492,7 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
     RayOut out;
     out.st[0] = out.st[1] = out.st[2] = out.st[3] = 0;
     if (valid) {
-        march_ray<S, K, MODE, EXACT>(tv, rp, io, ray, ow, dw, stack, out);
+        march_ray<S, K, MODE, EXACT, NT, DEFER>(tv, rp, io, ray, ow, dw, stack, out);
         if constexpr (MODE == kFwd) {
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) io.rgb[3 * ray + ch] = out.rgb[ch];

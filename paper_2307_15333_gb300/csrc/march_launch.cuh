@@ -3,45 +3,59 @@
 
 #include "march.cuh"
 
+#ifndef DOT_FWD_NT
+#define DOT_FWD_NT 128
+#endif
+
 namespace dot {
 
+// threads per block of large forward launches, and the blocks per SM they are built for
+constexpr int kFwdThreads = DOT_FWD_NT;
+constexpr int kFwdMinBlocks = 1024 / kFwdThreads;
+
+template <int NT>
 inline dim3 march_grid(const RaySource &rs) {
     if (rs.kind == DOT_RAYS_CAMERAS) {
-        const int ty = (rs.height + 15) / 16;
-        return dim3((unsigned)(rs.tiles_x * ty), (unsigned)rs.n_cams);
+        const int tx = (rs.width + CamTile<NT>::kW - 1) / CamTile<NT>::kW;
+        const int ty = (rs.height + CamTile<NT>::kH - 1) / CamTile<NT>::kH;
+        return dim3((unsigned)(tx * ty), (unsigned)rs.n_cams);
     }
-    return dim3((unsigned)((rs.n_rays + kMarchThreads - 1) / kMarchThreads));
+    return dim3((unsigned)((rs.n_rays + NT - 1) / NT));
 }
 
-// Blocks above which a forward launch uses the occupancy build: two full waves of 4 blocks on
-// every SM of the current device (152 SMs on a GB300).
-inline int64_t occupancy_blocks() {
+// Forward launches of at least two full waves of the occupancy build on every SM of the current
+// device (152 SMs on a GB300) use that build.
+inline int64_t occupancy_threads() {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return 2 * 4 * (int64_t)sms;
+    return 2 * 1024 * (int64_t)sms;
+}
+
+template <typename S, int K, int MODE, int MINB, int NT, bool DEFER>
+cudaError_t launch_nt(bool exact, const TreeView &tv, const RaySource &rs0, const RenderParams &rp,
+                      const RenderIO &io, cudaStream_t stream) {
+    RaySource rs = rs0;
+    rs.tiles_x = (rs.width + CamTile<NT>::kW - 1) / CamTile<NT>::kW;
+    const dim3 grid = march_grid<NT>(rs);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    if (exact)
+        march_kernel<S, K, MODE, true, MINB, NT, DEFER><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
+    else
+        march_kernel<S, K, MODE, false, MINB, NT, DEFER><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
+    return cudaGetLastError();
 }
 
 template <typename S, int K, int MODE>
 cudaError_t launch_sk(bool exact, const TreeView &tv, const RaySource &rs, const RenderParams &rp,
                       const RenderIO &io, cudaStream_t stream) {
-    const dim3 grid = march_grid(rs);
-    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    const bool occ = MODE == kFwd && (int64_t)grid.x * grid.y >= occupancy_blocks();
+    if (rs.n_rays <= 0) return cudaSuccess;
     if constexpr (MODE == kFwd) {
-        if (occ) {
-            if (exact)
-                march_kernel<S, K, MODE, true, 4><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
-            else
-                march_kernel<S, K, MODE, false, 4><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
-            return cudaGetLastError();
-        }
+        if (rs.n_rays >= occupancy_threads())
+            return launch_nt<S, K, MODE, kFwdMinBlocks, kFwdThreads, false>(exact, tv, rs, rp, io, stream);
     }
-    if (exact)
-        march_kernel<S, K, MODE, true, 1><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
-    else
-        march_kernel<S, K, MODE, false, 1><<<grid, kMarchThreads, 0, stream>>>(tv, rs, rp, io);
-    return cudaGetLastError();
+    constexpr bool defer = MODE == kFwd || MODE == kBwd;
+    return launch_nt<S, K, MODE, 1, kMarchThreads, defer>(exact, tv, rs, rp, io, stream);
 }
 
 template <typename S, int MODE>

@@ -1,0 +1,213 @@
+// train.cu -- the optimisation step of the training loop (Algorithm 1, optimization):
+//   * the MSE loss over stochastic ray samples (Sec. 4.1) and its gradient dL/dC, the input of
+//     the backward march;
+//   * one RMSProp update of every leaf's density and SH coefficients (Sec. 3.3; learning rates of
+//     Sec. 4.1), fused with zeroing the FP32 gradients for the next step.
+// Both are HBM-bound streams: RMSProp moves 4 + 4 + 4 (+ 4 + 4 + 4 written) bytes of FP32
+// gradient and mean-square state and 2 x storage bytes of parameter per coefficient.
+#include "internal.cuh"
+
+namespace dot {
+
+namespace {
+
+constexpr int kTrainThreads = 256;
+
+// grad[r][c] = 2 (rgb - target) / (3 R); loss_sum += sum (rgb - target)^2 / (3 R)
+__global__ void __launch_bounds__(kTrainThreads)
+mse_grad_kernel(const float *__restrict__ rgb, const float *__restrict__ target, int64_t n,
+                float inv, float *__restrict__ grad, double *__restrict__ loss_sum) {
+    __shared__ float s_part[kTrainThreads / 32];
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float e = rgb[i] - target[i];
+        grad[i] = 2.f * e * inv;
+        acc = fmaf(e, e, acc);
+    }
+    if (!loss_sum) return;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < kTrainThreads / 32; w++) b += s_part[w];
+        atomicAdd(loss_sum, (double)b * (double)inv);
+    }
+}
+
+struct Rms {
+    float lr, rho, one_minus_rho, eps;
+    int zero_grad;
+};
+
+__device__ __forceinline__ float rms_update(float p, float g, float &ms, const Rms &o) {
+    ms = fmaf(o.rho, ms, o.one_minus_rho * (g * g));
+    return p - __fdiv_rn(o.lr * g, sqrtf(ms) + o.eps);
+}
+
+// one coefficient per thread: entry i of a [rows][width] FP32 array, parameter at
+// row * pstride + column in the storage type
+template <typename S>
+__global__ void __launch_bounds__(kTrainThreads)
+rmsprop_scalar_kernel(S *__restrict__ param, int64_t pstride, float *__restrict__ grad,
+                      float *__restrict__ ms, int64_t rows, int width, Rms o) {
+    const int64_t n = rows * width;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t r = i / width;
+        const int c = (int)(i - r * width);
+        S *pp = param + r * pstride + c;
+        const float g = grad[i];
+        float m = ms[i];
+        const float p = rms_update(Storage<S>::to_f32(*pp), g, m, o);
+        ms[i] = m;
+        *pp = Storage<S>::from_f32(p);
+        if (o.zero_grad) grad[i] = 0.f;
+    }
+}
+
+// four consecutive coefficients per thread (width % 4 == 0 and 16-byte aligned arrays)
+template <typename S> struct Vec4;
+template <> struct Vec4<float> {
+    using T = float4;
+    static __device__ __forceinline__ void get(const T &v, float x[4]) { x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+    static __device__ __forceinline__ T make(const float x[4]) { return make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <> struct Vec4<__half> {
+    using T = uint2;
+    static __device__ __forceinline__ void get(const T &v, float x[4]) {
+        const __half2 a = *reinterpret_cast<const __half2 *>(&v.x), b = *reinterpret_cast<const __half2 *>(&v.y);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        x[0] = fa.x; x[1] = fa.y; x[2] = fb.x; x[3] = fb.y;
+    }
+    static __device__ __forceinline__ T make(const float x[4]) {
+        const __half2 a = __halves2half2(__float2half_rn(x[0]), __float2half_rn(x[1]));
+        const __half2 b = __halves2half2(__float2half_rn(x[2]), __float2half_rn(x[3]));
+        T v;
+        v.x = *reinterpret_cast<const unsigned *>(&a);
+        v.y = *reinterpret_cast<const unsigned *>(&b);
+        return v;
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    using T = uint2;
+    static __device__ __forceinline__ void get(const T &v, float x[4]) {
+        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&v.x);
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v.y);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        x[0] = fa.x; x[1] = fa.y; x[2] = fb.x; x[3] = fb.y;
+    }
+    static __device__ __forceinline__ T make(const float x[4]) {
+        const __nv_bfloat162 a = __halves2bfloat162(__float2bfloat16_rn(x[0]), __float2bfloat16_rn(x[1]));
+        const __nv_bfloat162 b = __halves2bfloat162(__float2bfloat16_rn(x[2]), __float2bfloat16_rn(x[3]));
+        T v;
+        v.x = *reinterpret_cast<const unsigned *>(&a);
+        v.y = *reinterpret_cast<const unsigned *>(&b);
+        return v;
+    }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(kTrainThreads)
+rmsprop_vec4_kernel(S *__restrict__ param, int64_t pstride, float *__restrict__ grad,
+                    float *__restrict__ ms, int64_t rows, int width, Rms o) {
+    using V = Vec4<S>;
+    const int q = width / 4;
+    const int64_t n = rows * q;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t r = i / q;
+        const int c = (int)(i - r * q) * 4;
+        float4 *g4 = reinterpret_cast<float4 *>(grad) + i;
+        float4 *m4 = reinterpret_cast<float4 *>(ms) + i;
+        typename V::T *pv = reinterpret_cast<typename V::T *>(param + r * pstride + c);
+        const float4 g = *g4;
+        float4 m = *m4;
+        float p[4];
+        V::get(*pv, p);
+        p[0] = rms_update(p[0], g.x, m.x, o);
+        p[1] = rms_update(p[1], g.y, m.y, o);
+        p[2] = rms_update(p[2], g.z, m.z, o);
+        p[3] = rms_update(p[3], g.w, m.w, o);
+        *m4 = m;
+        *pv = V::make(p);
+        if (o.zero_grad) *g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+int grid_for(int64_t n) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + kTrainThreads - 1) / kTrainThreads;
+    const int64_t cap = (int64_t)sms * 8;  // 8 resident blocks of 256 per SM, grid-stride beyond
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <typename S>
+cudaError_t rmsprop_array(S *param, int64_t pstride, float *grad, float *ms, int64_t rows,
+                          int width, const Rms &o, cudaStream_t s) {
+    if (rows == 0 || width == 0) return cudaSuccess;
+    const bool vec = width % 4 == 0 && pstride % 4 == 0 && aligned16(grad) && aligned16(ms) &&
+                     (reinterpret_cast<uintptr_t>(param) % (4 * sizeof(S))) == 0;
+    if (vec) {
+        const int64_t n = rows * (width / 4);
+        rmsprop_vec4_kernel<S><<<grid_for(n), kTrainThreads, 0, s>>>(param, pstride, grad, ms, rows, width, o);
+    } else {
+        const int64_t n = rows * width;
+        rmsprop_scalar_kernel<S><<<grid_for(n), kTrainThreads, 0, s>>>(param, pstride, grad, ms, rows, width, o);
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t rmsprop_s(void *sigma, void *sh, int64_t L, int K, int row_stride, float *grad_sigma,
+                      float *grad_sh, float *ms_sigma, float *ms_sh, const dot_rmsprop_opts &op,
+                      cudaStream_t s) {
+    Rms o;
+    o.rho = op.rho;
+    o.one_minus_rho = 1.f - op.rho;
+    o.eps = op.eps;
+    o.zero_grad = op.zero_grad;
+    o.lr = op.lr_sigma;
+    // the density vector [L] walked as rows of 4096 contiguous entries plus one shorter row
+    cudaError_t e = cudaSuccess;
+    const int64_t W = 4096;
+    const int64_t full = L / W, rest = L - full * W;
+    S *sg = reinterpret_cast<S *>(sigma);
+    if (full) e = rmsprop_array<S>(sg, W, grad_sigma, ms_sigma, full, (int)W, o, s);
+    if (e == cudaSuccess && rest)
+        e = rmsprop_array<S>(sg + full * W, W, grad_sigma + full * W, ms_sigma + full * W, 1,
+                             (int)rest, o, s);
+    if (e != cudaSuccess) return e;
+    o.lr = op.lr_sh;
+    return rmsprop_array<S>(reinterpret_cast<S *>(sh), row_stride, grad_sh, ms_sh, L, 3 * K, o, s);
+}
+
+}  // namespace
+
+cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad,
+                            double *loss_sum, cudaStream_t s) {
+    if (n_rays == 0) return cudaSuccess;
+    const int64_t n = 3 * n_rays;
+    const float inv = (float)(1.0 / (3.0 * (double)n_rays));
+    mse_grad_kernel<<<grid_for(n), kTrainThreads, 0, s>>>(rgb, target, n, inv, grad, loss_sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmsprop(int storage, void *sigma, void *sh, int64_t L, int K, int row_stride,
+                           float *grad_sigma, float *grad_sh, float *ms_sigma, float *ms_sh,
+                           const dot_rmsprop_opts &op, cudaStream_t s) {
+    switch (storage) {
+        case DOT_STORAGE_F32: return rmsprop_s<float>(sigma, sh, L, K, row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh, op, s);
+        case DOT_STORAGE_F16: return rmsprop_s<__half>(sigma, sh, L, K, row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh, op, s);
+        case DOT_STORAGE_BF16: return rmsprop_s<__nv_bfloat16>(sigma, sh, L, K, row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh, op, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dot

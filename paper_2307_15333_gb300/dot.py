@@ -38,7 +38,8 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_tree_get_info", "dot_tree_export", "dot_tree_import", "dot_tree_status",
                 "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
-                "dot_select_masks_noalloc", "dot_render_slots")
+                "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
+                "dot_rmsprop_step")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -124,6 +125,11 @@ class dot_refine_counts(ctypes.Structure):
                 ("n_capped", ctypes.c_int64)]
 
 
+class dot_rmsprop_opts(ctypes.Structure):
+    _fields_ = [("lr_sigma", ctypes.c_float), ("lr_sh", ctypes.c_float), ("rho", ctypes.c_float),
+                ("eps", ctypes.c_float), ("zero_grad", ctypes.c_int32)]
+
+
 class dot_leaf_array(ctypes.Structure):
     _fields_ = [("src", P), ("dst", P), ("width", ctypes.c_int32), ("merge", ctypes.c_int32)]
 
@@ -163,6 +169,8 @@ def lib() -> ctypes.CDLL:
         "dot_render_stats": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.POINTER(ctypes.c_int64), P],
         "dot_select_masks_noalloc": [P, P, ctypes.POINTER(dot_select_opts), P, P, P],
         "dot_render_slots": [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.POINTER(dot_render_opts), P, P],
+        "dot_mse_grad": [P, P, ctypes.c_int64, P, P, P],
+        "dot_rmsprop_step": [P, P, P, P, P, ctypes.POINTER(dot_rmsprop_opts), P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -526,6 +534,41 @@ def dot_render_slots(trees: Sequence[Octree], table: torch.Tensor, max_slots: in
     handles = (ctypes.c_void_p * len(trees))(*[t.handle.value for t in trees])
     _check(lib().dot_render_slots(handles, len(trees), _ptr(table), int(max_slots),
                                   ctypes.byref(opts), _ptr(work_counter), _stream(stream)))
+
+
+def rmsprop_opts(lr_sigma=0.1, lr_sh=0.01, rho=0.9, eps=1e-8, zero_grad=True) -> dot_rmsprop_opts:
+    """Defaults: the learning rates of Sec. 4.1; rho and eps, which the paper does not give,
+    take the usual RMSProp values."""
+    o = dot_rmsprop_opts()
+    o.lr_sigma, o.lr_sh, o.rho, o.eps = float(lr_sigma), float(lr_sh), float(rho), float(eps)
+    o.zero_grad = int(bool(zero_grad))
+    return o
+
+
+def dot_mse_grad(rgb: torch.Tensor, target: torch.Tensor, grad_rgb: torch.Tensor,
+                 loss_sum: Optional[torch.Tensor] = None, stream=None):
+    """grad_rgb = 2 (rgb - target) / 3R; loss_sum (float64 device scalar) += the MSE."""
+    R = rgb.numel() // 3
+    _need(rgb, torch.float32, 3 * R, "rgb")
+    _need(target, torch.float32, 3 * R, "target")
+    _need(grad_rgb, torch.float32, 3 * R, "grad_rgb")
+    if loss_sum is not None:
+        _need(loss_sum, torch.float64, 1, "loss_sum")
+    _check(lib().dot_mse_grad(_ptr(rgb), _ptr(target), R, _ptr(grad_rgb), _ptr(loss_sum),
+                              _stream(stream)))
+
+
+def dot_rmsprop_step(tree: Octree, grad_sigma: torch.Tensor, grad_sh: torch.Tensor,
+                     ms_sigma: torch.Tensor, ms_sh: torch.Tensor, opts: dot_rmsprop_opts,
+                     stream=None):
+    inf = tree.info()
+    L, K = inf.n_leaves, inf.n_coeffs
+    _need(grad_sigma, torch.float32, L, "grad_sigma")
+    _need(ms_sigma, torch.float32, L, "ms_sigma")
+    _need(grad_sh, torch.float32, L * 3 * K, "grad_sh")
+    _need(ms_sh, torch.float32, L * 3 * K, "ms_sh")
+    _check(lib().dot_rmsprop_step(tree.handle, _ptr(grad_sigma), _ptr(grad_sh), _ptr(ms_sigma),
+                                  _ptr(ms_sh), ctypes.byref(opts), _stream(stream)))
 
 
 def dot_tree_status(tree: Octree, stream=None) -> int:

@@ -1,0 +1,122 @@
+"""The DOT training loop (Algorithm 1) on top of the C ABI.
+
+One optimisation step on a batch of stochastic ray samples (Sec. 4.1):
+    forward render with the training signal fused (Sec. 3.1: Q accumulates over the epoch),
+    MSE loss and dL/dC (dot_mse_grad), backward march into FP32 gradients
+    (dot_render_backward), RMSProp update of every leaf fused with zeroing the gradients
+    (dot_rmsprop_step; Sec. 3.3, learning rates of Sec. 4.1).
+Every T epochs (Algorithm 1) the tree is refined from the accumulated signal: pruning with
+threshold tau (optionally recursive, merging parents upward while groups still qualify, the
+merged signal being the sum -- or max -- of the children's), then sampling of the top-gamma
+fraction (Sec. 3.2), with the RMSProp state carried through the refine (mean of merged children,
+copies for sampled children).
+
+Every step runs in libdot's kernels; this module only holds the device buffers and sequences the
+calls.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from . import dot
+
+
+class Trainer:
+    def __init__(self, tree: dot.Octree, opts: dot.dot_render_opts,
+                 rms: Optional[dot.dot_rmsprop_opts] = None,
+                 signal_mode: int = dot.DOT_SIGNAL_SUM_ALPHA, stream=None):
+        self.tree = tree
+        self.opts = dot.render_opts(background=tuple(opts.background), eps_T=opts.eps_T,
+                                    color_act=opts.color_act, signal_mode=signal_mode,
+                                    precision=opts.precision, max_steps=opts.max_steps)
+        self.rms = rms if rms is not None else dot.rmsprop_opts()
+        self.signal_mode = signal_mode
+        self.stream = stream
+        self.loss_sum = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self._batch = 0
+        self._alloc_leaf_state(zero_ms=True)
+
+    # ---- per-leaf state --------------------------------------------------------------------
+    def _alloc_leaf_state(self, zero_ms: bool):
+        inf = self.tree.info()
+        L, K = int(inf.n_leaves), int(inf.n_coeffs)
+        self.L, self.K = L, K
+        self.grad_sigma = torch.zeros(L, dtype=torch.float32, device="cuda")
+        self.grad_sh = torch.zeros(L, 3, K, dtype=torch.float32, device="cuda")
+        self.signal = torch.zeros(L, dtype=torch.float32, device="cuda")
+        if zero_ms:
+            self.ms_sigma = torch.zeros(L, dtype=torch.float32, device="cuda")
+            self.ms_sh = torch.zeros(L, 3, K, dtype=torch.float32, device="cuda")
+
+    def _buffers(self, R: int):
+        if self._batch != R:
+            self.rgb = torch.empty(R, 3, dtype=torch.float32, device="cuda")
+            self.grad_rgb = torch.empty(R, 3, dtype=torch.float32, device="cuda")
+            self._batch = R
+
+    # ---- Algorithm 1, optimization ---------------------------------------------------------
+    def step(self, rays: dot.dot_rays, target: torch.Tensor):
+        """One optimisation step on `rays` against `target` [R, 3]; the batch MSE is added to
+        self.loss_sum (device float64)."""
+        R = dot.n_rays_of(rays)
+        self._buffers(R)
+        s = self.stream
+        sig = self.signal if self.signal_mode != dot.DOT_SIGNAL_NONE else None
+        dot.dot_render_forward(self.tree, rays, self.opts, self.rgb, None, sig, stream=s)
+        dot.dot_mse_grad(self.rgb, target, self.grad_rgb, self.loss_sum, stream=s)
+        plain = dot.render_opts(background=tuple(self.opts.background), eps_T=self.opts.eps_T,
+                                color_act=self.opts.color_act, precision=self.opts.precision,
+                                max_steps=self.opts.max_steps)
+        dot.dot_render_backward(self.tree, rays, plain, self.grad_rgb, self.rgb,
+                                self.grad_sigma, self.grad_sh, stream=s)
+        dot.dot_rmsprop_step(self.tree, self.grad_sigma, self.grad_sh, self.ms_sigma,
+                             self.ms_sh, self.rms, stream=s)
+
+    # ---- Algorithm 1, pruning and sampling -------------------------------------------------
+    def refine(self, tau: float, gamma: float, depth_cap: int, recursive: bool = False,
+               prune_mode: int = dot.DOT_SELECT_THRESHOLD,
+               sample_mode: int = dot.DOT_SELECT_FRACTION) -> dict:
+        """Prunes leaves with signal <= tau (recursively when asked), then samples the top-gamma
+        fraction by the signal (Algorithm 1).  Returns the leaf counts of each pass."""
+        merge = dot.DOT_MERGE_MAX if self.signal_mode == dot.DOT_SIGNAL_MAX_WEIGHT else dot.DOT_MERGE_SUM
+        passes = []
+        while True:
+            pm, sm = self._marks(dot.select_opts(prune_mode, tau, dot.DOT_SELECT_NONE, 0.0))
+            plan = dot.dot_refine_plan(self.tree, pm, sm, depth_cap, stream=self.stream)
+            if plan["n_pruned_groups"] == 0:
+                break
+            self._apply(pm, sm, depth_cap, plan, merge)
+            passes.append(plan)
+            if not recursive:
+                break
+        pm, sm = self._marks(dot.select_opts(dot.DOT_SELECT_NONE, 0.0, sample_mode, gamma))
+        plan = dot.dot_refine_plan(self.tree, pm, sm, depth_cap, stream=self.stream)
+        if plan["n_sampled"] > 0:
+            self._apply(pm, sm, depth_cap, plan, merge)
+            passes.append(plan)
+        # a new stabilisation interval starts: fresh signal and gradients
+        self.grad_sigma = torch.zeros(self.L, dtype=torch.float32, device="cuda")
+        self.grad_sh = torch.zeros(self.L, 3, self.K, dtype=torch.float32, device="cuda")
+        self.signal = torch.zeros(self.L, dtype=torch.float32, device="cuda")
+        return {"passes": passes, "n_leaves": self.L, "n_nodes": self.tree.n_nodes}
+
+    def _marks(self, sel: dot.dot_select_opts):
+        pm = torch.empty(self.L, dtype=torch.uint8, device="cuda")
+        sm = torch.empty(self.L, dtype=torch.uint8, device="cuda")
+        dot.dot_select_masks(self.tree, self.signal, sel, pm, sm, stream=self.stream)
+        return pm, sm
+
+    def _apply(self, pm, sm, depth_cap, plan, merge):
+        Ln, K = plan["n_leaves"], self.K
+        lm = torch.empty(Ln, dtype=torch.int32, device="cuda")
+        ms_sigma = torch.empty(Ln, dtype=torch.float32, device="cuda")
+        ms_sh = torch.empty(Ln, 3, K, dtype=torch.float32, device="cuda")
+        signal = torch.empty(Ln, dtype=torch.float32, device="cuda")
+        aux = [(self.ms_sigma, ms_sigma, dot.DOT_MERGE_MEAN), (self.ms_sh, ms_sh, dot.DOT_MERGE_MEAN),
+               (self.signal, signal, merge)]
+        dot.dot_refine_prune(self.tree, pm, sm, depth_cap, lm, aux, stream=self.stream)
+        self.ms_sigma, self.ms_sh, self.signal = ms_sigma, ms_sh, signal
+        self.leaf_map = lm
+        self.L = Ln

@@ -1,0 +1,158 @@
+"""The training step on the GPU (MSE gradient, RMSProp fused with zeroing the gradients) and the
+Algorithm 1 loop (optimisation steps, then recursive pruning and sampling) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import seeded_inputs as si
+from helpers import assert_sums_close, oracle_side
+
+pytestmark = pytest.mark.gpu
+
+
+def _ulp(x, storage):
+    """Spacing of the storage format at |x|."""
+    x = np.abs(np.asarray(x, np.float64))
+    if storage == si.STORAGE_F32:
+        return np.spacing(x.astype(np.float32)).astype(np.float64)
+    if storage == si.STORAGE_F16:
+        return np.spacing(x.astype(np.float16)).astype(np.float64)
+    e = np.floor(np.log2(np.maximum(x, 2.0 ** -126)))
+    return 2.0 ** (e - 7)
+
+
+@pytest.mark.parametrize("R", [0, 1, 37, 4099, 70001])
+def test_mse_grad_matches_oracle(R):
+    import paper_2307_15333_gb300 as dot
+    rng = np.random.default_rng(R)
+    rgb = rng.random((R, 3)).astype(np.float32)
+    tgt = rng.random((R, 3)).astype(np.float32)
+    g = torch.full((R, 3), 7.0, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dot.dot.dot_mse_grad(torch.from_numpy(rgb).cuda(), torch.from_numpy(tgt).cuda(), g, loss)
+    torch.cuda.synchronize()
+    if R == 0:
+        assert float(loss) == 0.0
+        return
+    ref_loss, ref_g = oracle.mse(rgb, tgt)
+    np.testing.assert_allclose(g.cpu().numpy(), ref_g, rtol=1e-6, atol=1e-12)
+    assert float(loss) == pytest.approx(ref_loss, rel=1e-5)
+
+
+@pytest.mark.parametrize("storage,deg", [(st, d) for st in (si.STORAGE_F32, si.STORAGE_F16, si.STORAGE_BF16)
+                                         for d in range(4)])
+def test_rmsprop_matches_oracle(storage, deg):
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(60 + deg, max_depth=4, sh_degree=deg, storage=storage, n_prims=3)
+    tree = dot.octree_from_scene(scene)
+    L, K = tree.n_leaves, (deg + 1) ** 2
+    rng = np.random.default_rng(deg + 10 * storage)
+    gs = (rng.normal(size=L) * 0.1).astype(np.float32)
+    gsh = (rng.normal(size=(L, 3, K)) * 0.01).astype(np.float32)
+    gs[::7] = 0.0
+    ms_s = (rng.random(L) * 0.01).astype(np.float32)
+    ms_sh = (rng.random((L, 3, K)) * 1e-4).astype(np.float32)
+    ms_sh[::5] = 0.0
+    p_s = tree.sigma.float().cpu().numpy().astype(np.float64)
+    p_sh = tree.sh.float().cpu().numpy().astype(np.float64)
+    t_gs, t_gsh = torch.from_numpy(gs).cuda(), torch.from_numpy(gsh).cuda()
+    t_ms, t_msh = torch.from_numpy(ms_s).cuda(), torch.from_numpy(ms_sh).cuda()
+    opts = dot.dot.rmsprop_opts(lr_sigma=0.1, lr_sh=0.01, rho=0.9, eps=1e-8)
+    dot.dot.dot_rmsprop_step(tree, t_gs, t_gsh, t_ms, t_msh, opts)
+    torch.cuda.synchronize()
+    assert not t_gs.any() and not t_gsh.any()
+    for p0, g, m0, lr, got_p, got_m in ((p_s, gs, ms_s, 0.1, tree.sigma, t_ms),
+                                        (p_sh, gsh, ms_sh, 0.01, tree.sh, t_msh)):
+        ref_p, ref_m = oracle.rmsprop(p0, m0, g, lr, 0.9, 1e-8)
+        got_m = got_m.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got_m, ref_m, rtol=1e-6, atol=1e-30)
+        got_p = got_p.float().cpu().numpy().astype(np.float64)
+        upd = np.abs(ref_p - p0)
+        lim = 1e-6 * (np.abs(p0) + upd)
+        if storage != si.STORAGE_F32:
+            lim = lim + _ulp(ref_p, storage)
+        d = np.abs(got_p - ref_p)
+        assert (d <= lim).all(), f"{(d > lim).sum()} parameters beyond tolerance, worst {d.max():.3g}"
+    tree.free()
+
+
+def _oracle_remap(t, lm, a, merge):
+    return oracle.remap_leaf_values(t, lm, a, merge)
+
+
+def test_training_loop_matches_oracle():
+    """Three optimisation steps (forward with the fused SUM_ALPHA signal, MSE gradient, backward,
+    RMSProp) on an FP32 scene, then Algorithm 1's recursive pruning and top-gamma sampling, all on
+    the GPU through the Trainer, against the same sequence composed from the oracle."""
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.train import Trainer
+    scene = si.random_scene(70, max_depth=5, sh_degree=1, storage=si.STORAGE_F32, n_prims=3)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    bg = (1.0, 1.0, 1.0)
+    opts = dot.render_opts(background=bg, eps_T=0.0)
+    lr_s, lr_h, rho, eps = 0.1, 0.01, 0.9, 1e-3
+    tr = Trainer(tree, opts, dot.dot.rmsprop_opts(lr_s, lr_h, rho, eps),
+                 signal_mode=dot.dot.DOT_SIGNAL_SUM_ALPHA)
+    ms_s, ms_h = np.zeros_like(s64), np.zeros_like(h64)
+    S = np.zeros(s64.shape[0])
+    Sabs = np.zeros(s64.shape[0])
+    rng = np.random.default_rng(1)
+    for b in range(3):
+        o, d = si.random_rays(3000, 300 + b)
+        tgt = rng.random((3000, 3)).astype(np.float32)
+        rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+        tr.step(rays, torch.from_numpy(tgt).cuda())
+        # oracle: the same step, parameters rounded to the FP32 storage after the update
+        rgb, _, _ = oracle.render(t, lo, size, s64, h64, 1, o, d, bg=bg, eps_T=0.0, signal=S,
+                                  signal_mode=oracle.SIGNAL_SUM_ALPHA)
+        _, g = oracle.mse(rgb, tgt)
+        gs, gsh, _, _ = oracle.backward(t, lo, size, s64, h64, 1, o, d, g, bg=bg, eps_T=0.0)
+        s64, ms_s = oracle.rmsprop(s64, ms_s, gs, lr_s, rho, eps)
+        h64, ms_h = oracle.rmsprop(h64, ms_h, gsh, lr_h, rho, eps)
+        s64 = s64.astype(np.float32).astype(np.float64)
+        h64 = h64.astype(np.float32).astype(np.float64)
+    torch.cuda.synchronize()
+    assert tree.status() == 0
+    got_s = tree.sigma.cpu().numpy().astype(np.float64)
+    got_h = tree.sh.cpu().numpy().astype(np.float64)
+    # an FP32 gradient error dg moves an update by at most lr dg / eps (|g| << eps) and not at all
+    # once |g| >> eps; the FP32 gradients match to ~1e-5 of their summed magnitudes
+    np.testing.assert_allclose(got_s, s64, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(got_h, h64, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(tr.ms_sigma.cpu().numpy(), ms_s, rtol=1e-3, atol=1e-9)
+    sig = tr.signal.cpu().numpy().astype(np.float64)
+    assert_sums_close(sig, S, S, 1e-5, "signal")
+
+    # Algorithm 1 pruning (recursive) and sampling on the accumulated signal: tau and gamma are
+    # placed in gaps of the oracle's signal so that FP32 sums cannot flip a decision
+    pos = np.sort(S[S > 0])
+    assert pos.size > 20
+    gaps = [(pos[i + 1] - pos[i]) / pos[i + 1] for i in range(pos.size // 4, pos.size // 2)]
+    i = pos.size // 4 + int(np.argmax(gaps))
+    tau = 0.5 * (pos[i] + pos[i + 1])
+    nt, so, sho, S2, (ms_s2, ms_h2), passes = oracle.prune_recursive(
+        t, s64, h64, S.astype(np.float32), tau, d_cap=7, aux=(ms_s, ms_h))
+    L2 = nt["leaf_key"].size
+    order = np.lexsort((np.arange(L2), -S2))
+    k = max(1, int(np.ceil(0.05 * L2)))
+    while k < L2 and abs(S2[order[k - 1]] - S2[order[k]]) <= 1e-4 * abs(S2[order[k - 1]]):
+        k += 1
+    gamma = (k - 0.5) / L2
+    pm2, smk = oracle.select(S2.astype(np.float32), oracle.SELECT_NONE, 0.0,
+                             oracle.SELECT_FRACTION, gamma)
+    nt3, lm3, so3, sho3, cnt3 = oracle.refine(nt, so, sho, pm2, smk, 7)
+    res = tr.refine(tau, gamma, depth_cap=7, recursive=True)
+    assert [p["n_pruned_groups"] for p in res["passes"][:-1]] == [p["n_pruned_groups"] for p in passes]
+    ex = tree.export()
+    for key in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key"):
+        assert np.array_equal(ex[key], nt3[key]), key
+    np.testing.assert_array_equal(tr.leaf_map.cpu().numpy(), lm3)
+    np.testing.assert_allclose(ex["sigma"].astype(np.float64), so3, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(ex["sh"].astype(np.float64), sho3, rtol=1e-5, atol=1e-4)
+    ms3 = oracle.remap_leaf_values(nt, lm3, ms_s2, "mean")
+    np.testing.assert_allclose(tr.ms_sigma.cpu().numpy(), ms3, rtol=1e-3, atol=1e-9)
+    assert tr.L == nt3["leaf_key"].size and tr.grad_sigma.shape[0] == tr.L
+    tree.free()
