@@ -357,6 +357,31 @@ def median_cut(x, bits):
     return index, pal
 
 
+def canonicalize(tree, leaf_values=()):
+    """The canonical numbering of a tree's cells (the build's order: breadth first, Morton order
+    within a level), which is ascending key order since a key is 1 << 3l | morton code.  Nodes and
+    leaves are sorted by key (a library sort); child pointers and parents follow.  Returns
+    (new_tree, perm) with perm[new leaf] = old leaf, and the leaf_values arrays permuted."""
+    nk = np.asarray(tree["node_key"], np.uint64)
+    lk = np.asarray(tree["leaf_key"], np.uint64)
+    nperm = np.argsort(nk, kind="stable")
+    lperm = np.argsort(lk, kind="stable")
+    n_new = np.empty(nk.size, np.int64)
+    n_new[nperm] = np.arange(nk.size)
+    l_new = np.empty(lk.size, np.int64)
+    l_new[lperm] = np.arange(lk.size)
+    old_child = np.asarray(tree["child"], np.int64)[nperm]
+    child = np.where(old_child >= 0, n_new[np.maximum(old_child, 0)],
+                     -1 - l_new[np.maximum(-1 - old_child, 0)]).astype(np.int32)
+    npar = np.asarray(tree["node_parent"], np.int64)[nperm]
+    node_parent = np.where(npar >= 0, n_new[np.maximum(npar, 0)], -1).astype(np.int32)
+    leaf_parent = n_new[np.asarray(tree["leaf_parent"], np.int64)[lperm]].astype(np.int32)
+    new = {"n_nodes": nk.size, "n_leaves": lk.size, "child": child, "node_parent": node_parent,
+           "node_key": nk[nperm], "leaf_parent": leaf_parent, "leaf_key": lk[lperm]}
+    vals = [np.asarray(v)[lperm] for v in leaf_values]
+    return new, lperm.astype(np.int32), vals
+
+
 def key_level(keys) -> np.ndarray:
     """Level of each Morton key with a leading 1 bit (reads the key format, no method logic)."""
     k = np.asarray(keys, dtype=np.uint64)

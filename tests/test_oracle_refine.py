@@ -243,3 +243,54 @@ def test_remap_leaf_values_by_hand():
     assert lm.tolist() == list(range(8))
     s = np.arange(8, dtype=np.float64)
     np.testing.assert_array_equal(oracle.remap_leaf_values(t, lm, s), s)
+
+
+# ----------------------------------------------------------------------------------------------
+# canonical numbering after refines
+# ----------------------------------------------------------------------------------------------
+def _consistent(t):
+    """Every pointer agrees with the keys: child slot j of key k holds key (k << 3) | j."""
+    child, nk, lk = t["child"], t["node_key"], t["leaf_key"]
+    for n in range(nk.size):
+        for j in range(8):
+            c = int(child[n, j])
+            key = int(nk[c]) if c >= 0 else int(lk[-1 - c])
+            assert key == (int(nk[n]) << 3) | j
+            par = t["node_parent"][c] if c >= 0 else t["leaf_parent"][-1 - c]
+            assert par == n
+
+
+def test_canonical_form_of_a_built_tree_is_itself():
+    sc = si.random_scene(3, max_depth=4, sh_degree=0, n_prims=3)
+    t = oracle.scene_tree(sc)
+    new, perm, _ = oracle.canonicalize(t)
+    assert perm.tolist() == list(range(t["leaf_key"].size))
+    for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key"):
+        assert np.array_equal(new[k], t[k]), k
+
+
+def test_canonical_form_after_refines_is_sorted_and_consistent():
+    sc = si.random_scene(4, max_depth=4, sh_degree=1, n_prims=3)
+    t = oracle.scene_tree(sc)
+    L = t["leaf_key"].size
+    rng = np.random.default_rng(0)
+    sigma = rng.random(L)
+    sh = rng.normal(size=(L, 3, 4))
+    for r in range(3):
+        L = t["leaf_key"].size
+        pm = (rng.random(L) < 0.5).astype(np.uint8)
+        sm = (rng.random(L) < 0.1).astype(np.uint8)
+        t, lm, sigma, sh, _ = oracle.refine(t, sigma, sh, pm, sm, 7)
+    assert np.any(np.diff(t["leaf_key"].astype(np.int64)) < 0)       # refines append
+    new, perm, (s2, h2) = oracle.canonicalize(t, (sigma, sh))
+    assert np.all(np.diff(new["leaf_key"].astype(np.int64)) > 0)
+    assert np.all(np.diff(new["node_key"].astype(np.int64)) > 0)
+    assert new["node_key"][0] == 1 and new["node_parent"][0] == -1
+    _consistent(new)
+    np.testing.assert_array_equal(s2, sigma[perm])
+    # the same cells render the same: rays see identical segments and values
+    lo, size = oracle.root_of(sc)
+    o, d = si.random_rays(100, 5)
+    a, _, _ = oracle.render(t, lo, size, sigma, sh, 1, o, d)
+    b, _, _ = oracle.render(new, lo, size, s2, h2, 1, o, d)
+    np.testing.assert_array_equal(a, b)
