@@ -128,7 +128,11 @@ typedef struct {
     int32_t *leaf_parent;  /* device [n_leaves] */
     uint64_t *leaf_key;    /* device [n_leaves] */
     void *sigma;           /* device [n_leaves], storage type */
-    void *sh;              /* device [n_leaves][sh_row_stride], storage type */
+    void *sh;              /* device [n_leaves][sh_row_stride], storage type; NULL if compressed */
+    int32_t palette_bits;  /* 0, or the palette of a compressed tree has 2^palette_bits rows */
+    int32_t pad2_;
+    void *palette;         /* device [2^palette_bits][sh_row_stride], storage type, or NULL */
+    uint32_t *leaf_record; /* device [n_leaves]: density bits | palette row << 16, or NULL */
 } dot_tree_info;
 
 /* Host copy of a tree (checkpoint / import).  sh is [n_leaves][3K] without row padding. */
@@ -390,6 +394,34 @@ int dot_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *g
  */
 int dot_rmsprop_step(dot_tree *tree, float *grad_sigma, float *grad_sh, float *ms_sigma,
                      float *ms_sh, const dot_rmsprop_opts *opts, void *stream);
+
+/*
+ * dot_compress_sh -- the compressed model of Sec. 4.1: every leaf's SH coefficient row is replaced
+ * by one of 2^bits palette rows, found by median cut (Heckbert 1982) over the leaves' coefficient
+ * vectors: each of the bits rounds splits every box of two or more vectors at the median of its
+ * longest axis (largest max - min; ties to the lowest axis; members ordered by (value, leaf id),
+ * floor(m/2) to the lower child); a palette row is the mean of its box rounded to the storage
+ * type.  Each leaf then keeps one 32-bit record, its 16-bit density in the low half and its
+ * palette row in the high half, so rendering reads 4 bytes per segment plus a palette row.
+ * bits: 1..16; 16-bit storage only (DOT_ERR_UNSUPPORTED for FP32).  The quantiser runs on the
+ * host and the call synchronises the stream.  Afterwards forward renders, signals, statistics and
+ * slot tables read the records; dot_render_backward, dot_rmsprop_step, dot_refine_plan and
+ * dot_refine_prune return DOT_ERR_UNSUPPORTED; dot_tree_export writes the expanded coefficients.
+ */
+int dot_compress_sh(dot_tree *tree, int32_t bits, void *stream);
+
+/*
+ * dot_tree_canonicalize -- renumbers the tree's nodes and leaves into the build's canonical order
+ * (breadth first, Morton order within a level: ascending key order).  Refines (Eq. 3-4) append
+ * new cells at the end of the arrays; renumbering restores memory locality between neighbouring
+ * cells.  The cells and their values do not change, so renders are bit-identical.
+ * leaf_perm: device [L] int32 (written): the old id of each new leaf (compose with a refine's
+ * leaf_map as leaf_map[leaf_perm[u]]).  aux[n_aux]: per-leaf FP32 arrays [L][width] permuted the
+ * same way from src into dst (distinct buffers).  Works on compressed trees too.  Synchronises
+ * once per level; frees the old arrays (previous dot_tree_get_info pointers become invalid).
+ */
+int dot_tree_canonicalize(dot_tree *tree, int32_t *leaf_perm, const dot_leaf_array *aux,
+                          int32_t n_aux, void *stream);
 
 /*
  * dot_render_stats -- counts of the march for these rays (not part of any hot path): out[0] =

@@ -28,6 +28,9 @@ cudaError_t launch_march_signal(int storage, bool exact, const TreeView &tv, con
                                 const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
 cudaError_t launch_march_stats(int storage, bool exact, const TreeView &tv, const RaySource &rs,
                                const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
+cudaError_t compress_tree(TreeArrays &a, int bits, const DevAlloc &al, cudaStream_t s);
+cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevAlloc &alloc,
+                              int32_t *perm, const dot_leaf_array *aux, int n_aux, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad,
                             double *loss_sum, cudaStream_t s);
 cudaError_t launch_rmsprop(int storage, void *sigma, void *sh, int64_t L, int K, int row_stride,
@@ -63,6 +66,14 @@ int check_tree(const dot_tree *t) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaGetDevice");
     if (dev != t->device) return fail(DOT_ERR_INVALID_ARG, "the current device is not the tree's device");
+    return DOT_OK;
+}
+
+// calls that read or write per-leaf SH rows do not apply to a compressed tree
+int check_uncompressed(const dot_tree *t, const char *what) {
+    if (t->a.leaf_rec)
+        return fail(DOT_ERR_UNSUPPORTED, std::string(what) + ": the tree's SH rows are compressed "
+                                         "(rendering only)");
     return DOT_OK;
 }
 
@@ -110,7 +121,8 @@ dot::TreeView view_of(const dot_tree *t) {
     dot::TreeView tv;
     tv.child = t->a.child;
     tv.sigma = t->a.sigma;
-    tv.sh = t->a.sh;
+    tv.sh = t->a.leaf_rec ? t->a.palette : t->a.sh;
+    tv.rec = t->a.leaf_rec;
     tv.n_nodes = t->a.n_nodes;
     tv.n_leaves = t->a.n_leaves;
     tv.row_stride = t->a.row_stride;
@@ -265,6 +277,9 @@ int dot_tree_get_info(const dot_tree *t, dot_tree_info *info) {
     info->leaf_key = t->a.leaf_key;
     info->sigma = t->a.sigma;
     info->sh = t->a.sh;
+    info->palette_bits = t->a.palette_bits;
+    info->palette = t->a.palette;
+    info->leaf_record = t->a.leaf_rec;
     return DOT_OK;
 }
 
@@ -286,10 +301,25 @@ int dot_tree_export(const dot_tree *t, void *stream, int32_t *child, int32_t *no
     API_CK(cp(leaf_parent, a.leaf_parent, (size_t)a.n_leaves * 4), "export leaf_parent");
     API_CK(cp(leaf_key, a.leaf_key, (size_t)a.n_leaves * 8), "export leaf_key");
     API_CK(cp(sigma, a.sigma, (size_t)a.n_leaves * sb), "export sigma");
-    if (sh && a.n_leaves > 0)
+    if (sh && a.n_leaves > 0 && !a.leaf_rec)
         API_CK(cudaMemcpy2DAsync(sh, 3 * a.K * sb, a.sh, (size_t)a.row_stride * sb, 3 * a.K * sb,
                                  (size_t)a.n_leaves, cudaMemcpyDeviceToHost, s),
                "export sh");
+    if (sh && a.n_leaves > 0 && a.leaf_rec) {
+        // compressed: every leaf's coefficients are its palette row
+        const int64_t P = int64_t(1) << a.palette_bits;
+        std::vector<uint16_t> pal((size_t)P * a.row_stride);
+        std::vector<uint32_t> rec((size_t)a.n_leaves);
+        API_CK(cudaMemcpyAsync(pal.data(), a.palette, pal.size() * 2, cudaMemcpyDeviceToHost, s),
+               "export palette");
+        API_CK(cudaMemcpyAsync(rec.data(), a.leaf_rec, rec.size() * 4, cudaMemcpyDeviceToHost, s),
+               "export records");
+        API_CK(cudaStreamSynchronize(s), "export sync");
+        uint16_t *out = static_cast<uint16_t *>(sh);
+        for (int64_t v = 0; v < a.n_leaves; v++)
+            std::memcpy(out + v * 3 * a.K, pal.data() + (size_t)(rec[v] >> 16) * a.row_stride,
+                        (size_t)3 * a.K * 2);
+    }
     API_CK(cudaStreamSynchronize(s), "export sync");
     return DOT_OK;
 }
@@ -424,6 +454,7 @@ int dot_render_backward(const dot_tree *t, const dot_rays *rays, const dot_rende
     dot::RenderParams rp;
     bool exact = false;
     if ((rc = make_params(t, opts, rp, exact))) return rc;
+    if ((rc = check_uncompressed(t, "dot_render_backward"))) return rc;
     if (R > 0 && (!grad_rgb || !rgb || !grad_sigma || !grad_sh))
         return fail(DOT_ERR_INVALID_ARG, "grad_rgb, rgb, grad_sigma and grad_sh must not be NULL");
     if (rp.signal_mode != DOT_SIGNAL_NONE && !signal)
@@ -494,6 +525,7 @@ int dot_refine_plan(const dot_tree *t, const uint8_t *prune_mark, const uint8_t 
                     int32_t depth_cap, dot_refine_counts *out, void *stream) {
     int rc = check_tree(t);
     if (rc) return rc;
+    if ((rc = check_uncompressed(t, "dot_refine_plan"))) return rc;
     if (!prune_mark || !sample_mark || !out) return fail(DOT_ERR_INVALID_ARG, "masks and out must not be NULL");
     if (depth_cap < 1 || depth_cap > dot::kMaxLevels) return fail(DOT_ERR_INVALID_ARG, "depth_cap must be in [1, 16]");
     dot::RefinePlan plan{};
@@ -513,6 +545,7 @@ int dot_refine_prune(dot_tree *t, const uint8_t *prune_mark, const uint8_t *samp
                      void *stream) {
     int rc = check_tree(t);
     if (rc) return rc;
+    if ((rc = check_uncompressed(t, "dot_refine_prune"))) return rc;
     if (!prune_mark || !sample_mark || !leaf_map) return fail(DOT_ERR_INVALID_ARG, "masks and leaf_map must not be NULL");
     if (depth_cap < 1 || depth_cap > dot::kMaxLevels) return fail(DOT_ERR_INVALID_ARG, "depth_cap must be in [1, 16]");
     if (n_aux < 0 || (n_aux > 0 && !aux)) return fail(DOT_ERR_INVALID_ARG, "bad aux arrays");
@@ -615,6 +648,8 @@ extern "C" int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const v
         if (rc) return rc;
         if (trees[i]->a.storage != trees[0]->a.storage || trees[i]->a.sh_degree != trees[0]->a.sh_degree)
             return fail(DOT_ERR_INVALID_ARG, "served trees must share storage type and SH degree");
+        if ((trees[i]->a.leaf_rec != nullptr) != (trees[0]->a.leaf_rec != nullptr))
+            return fail(DOT_ERR_INVALID_ARG, "served trees must be all compressed or none");
         views[i] = view_of(trees[i]);
         if (trees[i]->a.max_level > max_level) max_level = trees[i]->a.max_level;
     }
@@ -647,6 +682,7 @@ extern "C" int dot_rmsprop_step(dot_tree *t, float *grad_sigma, float *grad_sh, 
     int rc = check_tree(t);
     if (rc) return rc;
     if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    if ((rc = check_uncompressed(t, "dot_rmsprop_step"))) return rc;
     if (t->a.n_leaves == 0) return DOT_OK;
     if (!grad_sigma || !grad_sh || !ms_sigma || !ms_sh)
         return fail(DOT_ERR_INVALID_ARG, "gradients and mean-square arrays are required");
@@ -657,5 +693,35 @@ extern "C" int dot_rmsprop_step(dot_tree *t, float *grad_sigma, float *grad_sh, 
                                t->a.row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh, *opts,
                                S(stream)),
            "dot_rmsprop_step");
+    return DOT_OK;
+}
+
+extern "C" int dot_compress_sh(dot_tree *t, int32_t bits, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (bits < 1 || bits > 16) return fail(DOT_ERR_INVALID_ARG, "bits must be in [1, 16]");
+    if (t->a.storage == DOT_STORAGE_F32)
+        return fail(DOT_ERR_UNSUPPORTED, "compression needs 16-bit leaf storage");
+    if ((rc = check_uncompressed(t, "dot_compress_sh"))) return rc;
+    API_CK(dot::compress_tree(t->a, bits, t->alloc, S(stream)), "dot_compress_sh");
+    return DOT_OK;
+}
+
+extern "C" int dot_tree_canonicalize(dot_tree *t, int32_t *leaf_perm, const dot_leaf_array *aux,
+                                     int32_t n_aux, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if (!leaf_perm && t->a.n_leaves > 0) return fail(DOT_ERR_INVALID_ARG, "leaf_perm is NULL");
+    if (n_aux < 0 || (n_aux > 0 && !aux)) return fail(DOT_ERR_INVALID_ARG, "bad aux arrays");
+    for (int i = 0; i < n_aux; i++)
+        if (!aux[i].src || !aux[i].dst || aux[i].width < 1 || aux[i].src == aux[i].dst)
+            return fail(DOT_ERR_INVALID_ARG, "aux array needs distinct src and dst and width >= 1");
+    dot::TreeArrays nw;
+    cudaError_t e = dot::canonicalize_tree(t->a, &nw, t->alloc, leaf_perm, aux, n_aux, S(stream));
+    if (e == cudaErrorInvalidValue)
+        return fail(DOT_ERR_INVALID_ARG, "the node table does not reach every node and leaf once");
+    API_CK(e, "dot_tree_canonicalize");
+    dot::free_tree_arrays(t->a, t->alloc, S(stream));
+    t->a = nw;
     return DOT_OK;
 }

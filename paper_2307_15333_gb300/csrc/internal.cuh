@@ -24,7 +24,8 @@ constexpr int kMaxPrimitives = 4096;
 struct TreeView {
     const int32_t *child;
     const void *sigma;
-    const void *sh;
+    const void *sh;            // SH rows, or the palette rows of a compressed tree
+    const uint32_t *rec;       // compressed tree: per-leaf (density bits | palette row << 16)
     int64_t n_nodes, n_leaves;
     int32_t row_stride;        // storage elements per SH row
     int32_t max_level;
@@ -97,17 +98,24 @@ inline int row_stride_elems(int storage, int K) {
 template <typename S> struct Storage;
 template <> struct Storage<float> {
     static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float from_bits16(uint32_t) { return 0.f; }  // no 16-bit form
     static __device__ __forceinline__ float from_f32(float x) { return x; }
     static __device__ __forceinline__ float to_f32(float x) { return x; }
 };
 template <> struct Storage<__half> {
     static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float from_bits16(uint32_t b) {
+        return __half2float(__ushort_as_half((unsigned short)(b & 0xffffu)));
+    }
     static __device__ __forceinline__ __half from_f32(float x) { return __float2half_rn(x); }
     static __device__ __forceinline__ float to_f32(__half x) { return __half2float(x); }
 };
 template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
         return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ float from_bits16(uint32_t b) {
+        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(b & 0xffffu)));
     }
     static __device__ __forceinline__ __nv_bfloat16 from_f32(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }

@@ -184,8 +184,10 @@ struct RayOut {
 // NT: threads of the block (stride of the shared path stack).  DEFER: shade each occupied
 // segment one occupied segment later, after prefetching its SH row into L1, so that the row's
 // latency overlaps the traversal in between (a gain for launches too small to hide latency by
-// occupancy).
-template <typename S, int K, int MODE, bool EXACT, int NT = kMarchThreads, bool DEFER = false>
+// occupancy).  COMP: the tree is compressed -- density and palette row come from one 32-bit
+// record per leaf and the rows are palette rows.
+template <typename S, int K, int MODE, bool EXACT, int NT = kMarchThreads, bool DEFER = false,
+          bool COMP = false>
 __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams &rp,
                                           const RenderIO &io, int64_t ray, const float ow[3],
                                           const float dw[3], int32_t *stack, RayOut &out) {
@@ -280,10 +282,10 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     // colour of one occupied segment (weight w, transmittance after it Tn, length delta):
     // C += w c; the backward also scatters dL/dsigma and dL/dSH for it.  Segments are shaded in
     // march order, so C is the prefix sum C_{<=i} the backward needs.
-    auto shade = [&](int32_t lf, float w, float Tn, float delta) {
+    auto shade = [&](int32_t lf, int64_t row, float w, float Tn, float delta) {
         if constexpr (MODE == kFwd || MODE == kBwd) {
             float z[3], col[3];
-            leaf_z<S, K>(shp + (int64_t)lf * tv.row_stride, Y, z);
+            leaf_z<S, K>(shp + row * tv.row_stride, Y, z);
 #pragma unroll
             for (int ch = 0; ch < 3; ch++)
                 col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
@@ -325,6 +327,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         }
     };
     int32_t p_leaf = -1;  // deferred occupied segment (DEFER)
+    int64_t p_row = 0;
     float p_w = 0.f, p_Tn = 0.f, p_delta = 0.f;
 
     PT t = tn;
@@ -344,7 +347,16 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             break;
         }
         ++steps;
-        const float sv = Storage<S>::load(sigma + leaf);
+        float sv;
+        int64_t row;  // SH row of the leaf: its own, or its palette entry
+        if constexpr (COMP) {
+            const uint32_t w = __ldg(tv.rec + leaf);
+            sv = Storage<S>::from_bits16(w);
+            row = w >> 16;
+        } else {
+            sv = Storage<S>::load(sigma + leaf);
+            row = leaf;
+        }
         const int cs = 1 << (kGridBits - level);
         int lo_g[3];
         PT te[3];
@@ -398,14 +410,15 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             const float w = T * alpha;
             if constexpr (MODE == kFwd || MODE == kBwd) {
                 if constexpr (DEFER) {
-                    prefetch_row<S, K>(shp + (int64_t)leaf * tv.row_stride);
-                    if (p_leaf >= 0) shade(p_leaf, p_w, p_Tn, p_delta);
+                    prefetch_row<S, K>(shp + row * tv.row_stride);
+                    if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
                     p_leaf = leaf;
+                    p_row = row;
                     p_w = w;
                     p_Tn = T * e;
                     p_delta = delta;
                 } else {
-                    shade(leaf, w, T * e, delta);
+                    shade(leaf, row, w, T * e, delta);
                 }
             }
             if (MODE != kStats && io.signal != nullptr) {
@@ -422,7 +435,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         level = next_level;
     }
     if constexpr (DEFER && (MODE == kFwd || MODE == kBwd)) {
-        if (p_leaf >= 0) shade(p_leaf, p_w, p_Tn, p_delta);
+        if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) out.rgb[ch] = fmaf(T, rp.bg[ch], C[ch]);
@@ -460,7 +473,8 @@ template <int NT> struct CamTile {
 // threads: at most 64 registers, 32 warps per SM, for launches large enough to fill the GPU
 // several times over; a single block's worth for small launches, whose time is the longest
 // ray's latency).
-template <typename S, int K, int MODE, bool EXACT, int MINB, int NT = kMarchThreads, bool DEFER = false>
+template <typename S, int K, int MODE, bool EXACT, int MINB, int NT = kMarchThreads,
+          bool DEFER = false, bool COMP = false>
 __global__ void __launch_bounds__(NT, MINB)
 march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
     __shared__ int32_t s_stack[kMaxLevels * NT];
@@ -492,7 +506,7 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
     RayOut out;
     out.st[0] = out.st[1] = out.st[2] = out.st[3] = 0;
     if (valid) {
-        march_ray<S, K, MODE, EXACT, NT, DEFER>(tv, rp, io, ray, ow, dw, stack, out);
+        march_ray<S, K, MODE, EXACT, NT, DEFER, COMP>(tv, rp, io, ray, ow, dw, stack, out);
         if constexpr (MODE == kFwd) {
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) io.rgb[3 * ray + ch] = out.rgb[ch];

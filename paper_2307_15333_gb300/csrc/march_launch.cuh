@@ -32,7 +32,7 @@ inline int64_t occupancy_threads() {
     return 2 * 1024 * (int64_t)sms;
 }
 
-template <typename S, int K, int MODE, int MINB, int NT, bool DEFER>
+template <typename S, int K, int MODE, int MINB, int NT, bool DEFER, bool COMP = false>
 cudaError_t launch_nt(bool exact, const TreeView &tv, const RaySource &rs0, const RenderParams &rp,
                       const RenderIO &io, cudaStream_t stream) {
     RaySource rs = rs0;
@@ -40,22 +40,23 @@ cudaError_t launch_nt(bool exact, const TreeView &tv, const RaySource &rs0, cons
     const dim3 grid = march_grid<NT>(rs);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     if (exact)
-        march_kernel<S, K, MODE, true, MINB, NT, DEFER><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
+        march_kernel<S, K, MODE, true, MINB, NT, DEFER, COMP><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
     else
-        march_kernel<S, K, MODE, false, MINB, NT, DEFER><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
+        march_kernel<S, K, MODE, false, MINB, NT, DEFER, COMP><<<grid, NT, 0, stream>>>(tv, rs, rp, io);
     return cudaGetLastError();
 }
 
-template <typename S, int K, int MODE>
+// COMP: forward renders of a compressed tree (density and palette row from the leaf records)
+template <typename S, int K, int MODE, bool COMP = false>
 cudaError_t launch_sk(bool exact, const TreeView &tv, const RaySource &rs, const RenderParams &rp,
                       const RenderIO &io, cudaStream_t stream) {
     if (rs.n_rays <= 0) return cudaSuccess;
     if constexpr (MODE == kFwd) {
         if (rs.n_rays >= occupancy_threads())
-            return launch_nt<S, K, MODE, kFwdMinBlocks, kFwdThreads, false>(exact, tv, rs, rp, io, stream);
+            return launch_nt<S, K, MODE, kFwdMinBlocks, kFwdThreads, false, COMP>(exact, tv, rs, rp, io, stream);
     }
     constexpr bool defer = MODE == kFwd || MODE == kBwd;
-    return launch_nt<S, K, MODE, 1, kMarchThreads, defer>(exact, tv, rs, rp, io, stream);
+    return launch_nt<S, K, MODE, 1, kMarchThreads, defer, COMP>(exact, tv, rs, rp, io, stream);
 }
 
 template <typename S, int MODE>

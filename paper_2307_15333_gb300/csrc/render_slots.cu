@@ -23,7 +23,7 @@ struct SlotHeader {
     int64_t total_tiles;
 };
 
-template <typename S, int K, bool EXACT>
+template <typename S, int K, bool EXACT, bool COMP>
 __global__ void __launch_bounds__(kMarchThreads, 4)
 slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots, RenderParams rp,
              unsigned long long *__restrict__ counter, uint32_t *status) {
@@ -64,7 +64,8 @@ slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots,
             float ow[3], dw[3];
             camera_ray(&sl->camera, px, py, ow, dw);
             RayOut out;
-            march_ray<S, K, kFwd, EXACT>(trees.t[tr], rp, io, 0, ow, dw, stack, out);
+            march_ray<S, K, kFwd, EXACT, kMarchThreads, false, COMP>(trees.t[tr], rp, io, 0, ow,
+                                                                      dw, stack, out);
             float *dst = sl->out + ((int64_t)py * W + px) * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) dst[ch] = out.rgb[ch];
@@ -72,7 +73,7 @@ slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots,
     }
 }
 
-template <typename S, int K, bool EXACT>
+template <typename S, int K, bool EXACT, bool COMP>
 cudaError_t launch_slots_sk(const SlotTrees &trees, const void *table, int32_t max_slots,
                             const RenderParams &rp, unsigned long long *counter, uint32_t *status,
                             int grid, cudaStream_t s) {
@@ -80,23 +81,26 @@ cudaError_t launch_slots_sk(const SlotTrees &trees, const void *table, int32_t m
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slots_kernel<S, K, EXACT>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slots_kernel<S, K, EXACT, COMP>,
                                                       kMarchThreads, 0);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
-    slots_kernel<S, K, EXACT><<<grid, kMarchThreads, 0, s>>>(
+    slots_kernel<S, K, EXACT, COMP><<<grid, kMarchThreads, 0, s>>>(
         trees, reinterpret_cast<const char *>(table), max_slots, rp, counter, status);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_slots_s(int deg, bool exact, const SlotTrees &trees, const void *table,
+cudaError_t launch_slots_s(int deg, bool exact, bool comp, const SlotTrees &trees, const void *table,
                            int32_t max_slots, const RenderParams &rp, unsigned long long *counter,
                            uint32_t *status, int grid, cudaStream_t s) {
 #define DOT_SLOTS_CASE(D, KK)                                                                    \
     case D:                                                                                      \
-        return exact ? launch_slots_sk<S, KK, true>(trees, table, max_slots, rp, counter, status, grid, s) \
-                     : launch_slots_sk<S, KK, false>(trees, table, max_slots, rp, counter, status, grid, s);
+        if (comp)                                                                                \
+            return exact ? launch_slots_sk<S, KK, true, true>(trees, table, max_slots, rp, counter, status, grid, s) \
+                         : launch_slots_sk<S, KK, false, true>(trees, table, max_slots, rp, counter, status, grid, s); \
+        return exact ? launch_slots_sk<S, KK, true, false>(trees, table, max_slots, rp, counter, status, grid, s) \
+                     : launch_slots_sk<S, KK, false, false>(trees, table, max_slots, rp, counter, status, grid, s);
     switch (deg) {
         DOT_SLOTS_CASE(0, 1)
         DOT_SLOTS_CASE(1, 4)
@@ -114,14 +118,15 @@ cudaError_t launch_render_slots(int storage, int deg, bool exact, const TreeView
                                 const RenderParams &rp, unsigned long long *counter,
                                 uint32_t *status, int grid, cudaStream_t s) {
     SlotTrees trees{};
+    const bool comp = n_trees > 0 && views[0].rec != nullptr;
     for (int i = 0; i < n_trees; i++) trees.t[i] = views[i];
     trees.n = n_trees;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     switch (storage) {
-        case DOT_STORAGE_F32: return launch_slots_s<float>(deg, exact, trees, table, max_slots, rp, counter, status, grid, s);
-        case DOT_STORAGE_F16: return launch_slots_s<__half>(deg, exact, trees, table, max_slots, rp, counter, status, grid, s);
-        case DOT_STORAGE_BF16: return launch_slots_s<__nv_bfloat16>(deg, exact, trees, table, max_slots, rp, counter, status, grid, s);
+        case DOT_STORAGE_F32: return launch_slots_s<float>(deg, exact, false, trees, table, max_slots, rp, counter, status, grid, s);
+        case DOT_STORAGE_F16: return launch_slots_s<__half>(deg, exact, comp, trees, table, max_slots, rp, counter, status, grid, s);
+        case DOT_STORAGE_BF16: return launch_slots_s<__nv_bfloat16>(deg, exact, comp, trees, table, max_slots, rp, counter, status, grid, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -35,7 +35,12 @@ struct TreeArrays {
     int32_t *leaf_parent = nullptr;
     uint64_t *leaf_key = nullptr;
     void *sigma = nullptr;
-    void *sh = nullptr;
+    void *sh = nullptr;            // [L][row_stride]; null once the SH rows are compressed
+    // compressed SH (16-bit storage only): palette [2^palette_bits][row_stride] and one 32-bit
+    // record per leaf, the density's 16 bits in the low half and the palette row in the high half
+    void *palette = nullptr;
+    uint32_t *leaf_rec = nullptr;
+    int palette_bits = 0;
 };
 
 inline void free_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStream_t s) {
@@ -46,6 +51,11 @@ inline void free_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStream_t s) 
     al.release(a.leaf_key, s);
     al.release(a.sigma, s);
     al.release(a.sh, s);
+    al.release(a.palette, s);
+    al.release(a.leaf_rec, s);
+    a.palette = nullptr;
+    a.leaf_rec = nullptr;
+    a.palette_bits = 0;
     a.child = a.node_parent = a.leaf_parent = nullptr;
     a.node_key = a.leaf_key = nullptr;
     a.sigma = a.sh = nullptr;

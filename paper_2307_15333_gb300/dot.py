@@ -39,7 +39,7 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
-                "dot_rmsprop_step")
+                "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -85,7 +85,8 @@ class dot_tree_info(ctypes.Structure):
                 ("sh_row_stride", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("center", ctypes.c_float * 3), ("half_size", ctypes.c_float),
                 ("child", P), ("node_parent", P), ("node_key", P), ("leaf_parent", P),
-                ("leaf_key", P), ("sigma", P), ("sh", P)]
+                ("leaf_key", P), ("sigma", P), ("sh", P), ("palette_bits", ctypes.c_int32),
+                ("pad2_", ctypes.c_int32), ("palette", P), ("leaf_record", P)]
 
 
 class dot_host_tree(ctypes.Structure):
@@ -171,6 +172,8 @@ def lib() -> ctypes.CDLL:
         "dot_render_slots": [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.POINTER(dot_render_opts), P, P],
         "dot_mse_grad": [P, P, ctypes.c_int64, P, P, P],
         "dot_rmsprop_step": [P, P, P, P, P, ctypes.POINTER(dot_rmsprop_opts), P],
+        "dot_compress_sh": [P, ctypes.c_int32, P],
+        "dot_tree_canonicalize": [P, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -265,9 +268,34 @@ class Octree:
         return _view(inf.sigma, (inf.n_leaves,), _TORCH_OF_STORAGE[inf.storage], self)
 
     @property
+    def palette_bits(self) -> int:
+        return int(self.info().palette_bits)
+
+    @property
+    def palette_index(self) -> torch.Tensor:
+        """[L] int64 palette row of every leaf of a compressed tree."""
+        inf = self.info()
+        if not inf.palette_bits:
+            raise ValueError("the tree is not compressed")
+        rec = _view(inf.leaf_record, (inf.n_leaves,), torch.int32, self)
+        return (rec.to(torch.int64) >> 16) & 0xFFFF
+
+    @property
+    def palette(self) -> torch.Tensor:
+        """[2^bits, 3, K] view of the palette of a compressed tree."""
+        inf = self.info()
+        if not inf.palette_bits:
+            raise ValueError("the tree is not compressed")
+        rows = _view(inf.palette, (1 << inf.palette_bits, inf.sh_row_stride),
+                     _TORCH_OF_STORAGE[inf.storage], self)
+        return rows[:, : 3 * inf.n_coeffs].unflatten(1, (3, inf.n_coeffs))
+
+    @property
     def sh_rows(self) -> torch.Tensor:
         """[L, row_stride] padded rows."""
         inf = self.info()
+        if inf.palette_bits:
+            raise ValueError("the tree is compressed: see palette and palette_index")
         return _view(inf.sh, (inf.n_leaves, inf.sh_row_stride), _TORCH_OF_STORAGE[inf.storage], self)
 
     @property
@@ -569,6 +597,26 @@ def dot_rmsprop_step(tree: Octree, grad_sigma: torch.Tensor, grad_sh: torch.Tens
     _need(ms_sh, torch.float32, L * 3 * K, "ms_sh")
     _check(lib().dot_rmsprop_step(tree.handle, _ptr(grad_sigma), _ptr(grad_sh), _ptr(ms_sigma),
                                   _ptr(ms_sh), ctypes.byref(opts), _stream(stream)))
+
+
+def dot_compress_sh(tree: Octree, bits: int, stream=None):
+    """Median-cut palette of 2^bits SH rows (the compressed model of Sec. 4.1); synchronises."""
+    _check(lib().dot_compress_sh(tree.handle, int(bits), _stream(stream)))
+
+
+def dot_tree_canonicalize(tree: Octree, leaf_perm: torch.Tensor, aux: Sequence = (),
+                          stream=None):
+    """Renumbers the tree in canonical (breadth-first Morton) order; leaf_perm [L] int32 receives
+    the old id of every new leaf; aux: (src [L, w] f32, dst [L, w] f32) pairs permuted alike."""
+    L = tree.n_leaves
+    _need(leaf_perm, torch.int32, L, "leaf_perm")
+    arr = (dot_leaf_array * max(1, len(aux)))()
+    for i, (src, dst) in enumerate(aux):
+        w = src.numel() // L if L else 1
+        _need(src, torch.float32, L * w, "aux src")
+        _need(dst, torch.float32, L * w, "aux dst")
+        arr[i].src, arr[i].dst, arr[i].width, arr[i].merge = src.data_ptr(), dst.data_ptr(), w, 0
+    _check(lib().dot_tree_canonicalize(tree.handle, _ptr(leaf_perm), arr, len(aux), _stream(stream)))
 
 
 def dot_tree_status(tree: Octree, stream=None) -> int:

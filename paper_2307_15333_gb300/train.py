@@ -77,9 +77,10 @@ class Trainer:
     # ---- Algorithm 1, pruning and sampling -------------------------------------------------
     def refine(self, tau: float, gamma: float, depth_cap: int, recursive: bool = False,
                prune_mode: int = dot.DOT_SELECT_THRESHOLD,
-               sample_mode: int = dot.DOT_SELECT_FRACTION) -> dict:
+               sample_mode: int = dot.DOT_SELECT_FRACTION, canonical: bool = False) -> dict:
         """Prunes leaves with signal <= tau (recursively when asked), then samples the top-gamma
-        fraction by the signal (Algorithm 1).  Returns the leaf counts of each pass."""
+        fraction by the signal (Algorithm 1); with `canonical` the tree is then renumbered in
+        breadth-first Morton order (the RMSProp state follows).  Returns the plan of each pass."""
         merge = dot.DOT_MERGE_MAX if self.signal_mode == dot.DOT_SIGNAL_MAX_WEIGHT else dot.DOT_MERGE_SUM
         passes = []
         while True:
@@ -96,6 +97,13 @@ class Trainer:
         if plan["n_sampled"] > 0:
             self._apply(pm, sm, depth_cap, plan, merge)
             passes.append(plan)
+        if canonical:
+            perm = torch.empty(self.L, dtype=torch.int32, device="cuda")
+            ms_sigma, ms_sh = torch.empty_like(self.ms_sigma), torch.empty_like(self.ms_sh)
+            dot.dot_tree_canonicalize(self.tree, perm, [(self.ms_sigma, ms_sigma),
+                                                        (self.ms_sh, ms_sh)], stream=self.stream)
+            self.ms_sigma, self.ms_sh = ms_sigma, ms_sh
+            self.leaf_perm = perm
         # a new stabilisation interval starts: fresh signal and gradients
         self.grad_sigma = torch.zeros(self.L, dtype=torch.float32, device="cuda")
         self.grad_sh = torch.zeros(self.L, 3, self.K, dtype=torch.float32, device="cuda")
