@@ -180,8 +180,9 @@ def oracle_baseline(scene, cams, budget_s: float, threads: int):
     t0 = time.perf_counter()
     oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
     dt = time.perf_counter() - t0
+    which = "every pixel" if stride == 1 else f"every {stride}-th pixel"
     return {"value": o.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": f"every {stride}th pixel of the first {n_views} 800x800 views "
+            "sample": f"{which} of the {n_views} 800x800 views "
                       f"({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
 
 
@@ -284,7 +285,8 @@ def measure_training(scene, cams, steps: int):
     refine_ms = (time.perf_counter() - t0) * 1e3
     out = {"value": BATCH * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "iters_per_s": n / (ms / 1e3),
            "ms_per_iter": ms / n, "batch_rays": BATCH, "iters": n, "mean_batch_mse": loss,
-           "leaves": L0, "step": "fwd+signal, mse grad, bwd, rmsprop(all leaves)+zero grad",
+           "leaves": L0, "step": "fwd+signal, mse grad, bwd (+touched flags), sparse rmsprop (touched leaves, "
+                   "deferred decay)+zero grad",
            "refine": {"ms": refine_ms, "tau": q, "gamma": 0.05, "recursive": True,
                       "pruned_groups_per_pass": [p["n_pruned_groups"] for p in res["passes"]],
                       "leaves_after": res["n_leaves"]}}
@@ -488,6 +490,11 @@ def run_dot(args):
     value = R * args.steps * ws / (total_ms / 1e3) / 1e6
     mean_launch_s = statistics.mean(launch_ms) / 1e3
     assert tree.status() == 0
+    # distinct occupied leaves one launch touches (a max-weight signal pass, not timed)
+    touched = torch.zeros(L, dtype=torch.float32, device="cuda")
+    dot.dot_accumulate_signal(tree, rays, opts, dot.dot.DOT_SIGNAL_MAX_WEIGHT, touched)
+    u_leaf = int(torch.count_nonzero(touched))
+    del touched
 
     # ---- forward + backward on 2^16-ray batches (fixed synthetic dL/dC) ----
     nb = 8
@@ -587,11 +594,13 @@ def run_dot(args):
                 "alg_bytes_per_launch": alg_bytes,
                 "per_unit": {"occupied_segment_B": P + 4, "empty_segment_B": bs + 4,
                              "ray_output_B": 12},
-                "segments_per_ray": seg / R, "occupied_per_ray": occ / R}
+                "segments_per_ray": seg / R, "occupied_per_ray": occ / R,
+                "occupied_leaves_touched": u_leaf}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_baseline(scene, cams, args.cpu_seconds, os.cpu_count() or 1)
+        cpu["single_thread"] = oracle_baseline(scene, cams, 2.0, 1)
 
     line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -290,11 +290,13 @@ int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const void *table,
  *   dL/dsh[v][ch][k] += g_ch w_i act'(z_ch) Y_k,
  *   dL/dsigma[v]     += [sigma_v > 0] delta_i sum_ch g_ch (T_{i+1} c_ch - (C_ch - C_{<=i,ch})).
  * grad_rgb, rgb: device [R][3] (rgb = this tree's forward output for the same rays and opts);
- * grad_sigma: device [L] float (+=); grad_sh: device [L][3][K] float (+=); signal as forward.
+ * grad_sigma: device [L] float (+=); grad_sh: device [L][3][K] float (+=); signal as forward;
+ * touched: device [L] uint8 or NULL -- set to 1 for every leaf the backward gives a gradient
+ * (an occupied segment of some ray), for dot_rmsprop_step_sparse.
  */
 int dot_render_backward(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
                         const float *grad_rgb, const float *rgb, float *grad_sigma,
-                        float *grad_sh, float *signal, void *stream);
+                        float *grad_sh, float *signal, uint8_t *touched, void *stream);
 
 /*
  * dot_accumulate_signal -- the per-leaf training signal of Sec. 3.1 (Algorithm 1, optimization
@@ -394,6 +396,30 @@ int dot_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *g
  */
 int dot_rmsprop_step(dot_tree *tree, float *grad_sigma, float *grad_sh, float *ms_sigma,
                      float *ms_sh, const dot_rmsprop_opts *opts, void *stream);
+
+/*
+ * dot_rmsprop_step_sparse -- dot_rmsprop_step restricted to the leaves whose `touched` flag is set
+ * (dot_render_backward sets it for every leaf it gives a gradient), with the same results up to
+ * FP32 rounding.  A leaf nobody touched has zero gradients, so the dense update would only
+ * multiply its mean squares by rho; that decay is deferred and applied as rho^k for the k steps
+ * it sat out, the next time the leaf is touched or by dot_rmsprop_flush.
+ * touched: device [L] uint8, read and cleared; last_step: device [L] int32, the step up to which
+ * each leaf's mean squares are current (zeros before the first step); step: this step's number
+ * (1, 2, ...; increasing by one per call); work: device int32 [L + 1] scratch owned by the
+ * caller (the list of touched leaves and its count).  Gradients of touched leaves are zeroed
+ * when zero_grad is set; the others are zero already.
+ */
+int dot_rmsprop_step_sparse(dot_tree *tree, float *grad_sigma, float *grad_sh, float *ms_sigma,
+                            float *ms_sh, uint8_t *touched, int32_t *last_step, int32_t step,
+                            int32_t *work, const dot_rmsprop_opts *opts, void *stream);
+
+/*
+ * dot_rmsprop_flush -- applies every deferred decay up to step `step`:
+ * ms <- rho^(step - last_step) ms and last_step <- step for every leaf (before reading the mean
+ * squares, refining the tree or switching to dot_rmsprop_step).
+ */
+int dot_rmsprop_flush(dot_tree *tree, float *ms_sigma, float *ms_sh, int32_t *last_step,
+                      int32_t step, const dot_rmsprop_opts *opts, void *stream);
 
 /*
  * dot_compress_sh -- the compressed model of Sec. 4.1: every leaf's SH coefficient row is replaced

@@ -29,6 +29,13 @@ cudaError_t launch_march_signal(int storage, bool exact, const TreeView &tv, con
 cudaError_t launch_march_stats(int storage, bool exact, const TreeView &tv, const RaySource &rs,
                                const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
 cudaError_t compress_tree(TreeArrays &a, int bits, const DevAlloc &al, cudaStream_t s);
+cudaError_t launch_rmsprop_sparse(int storage, void *sigma, void *sh, int64_t L, int K,
+                                  int row_stride, float *grad_sigma, float *grad_sh,
+                                  float *ms_sigma, float *ms_sh, uint8_t *touched, int32_t *last,
+                                  int32_t step, int32_t *work, const dot_rmsprop_opts &op,
+                                  cudaStream_t s);
+cudaError_t launch_rmsprop_flush(int64_t L, int K, float *ms_sigma, float *ms_sh, int32_t *last,
+                                 int32_t step, float rho, cudaStream_t s);
 cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevAlloc &alloc,
                               int32_t *perm, const dot_leaf_array *aux, int n_aux, cudaStream_t s);
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad,
@@ -445,7 +452,7 @@ int dot_render_forward(const dot_tree *t, const dot_rays *rays, const dot_render
 
 int dot_render_backward(const dot_tree *t, const dot_rays *rays, const dot_render_opts *opts,
                         const float *grad_rgb, const float *rgb, float *grad_sigma,
-                        float *grad_sh, float *signal, void *stream) {
+                        float *grad_sh, float *signal, uint8_t *touched, void *stream) {
     int rc = check_tree(t);
     if (rc) return rc;
     dot::RaySource rs;
@@ -467,6 +474,7 @@ int dot_render_backward(const dot_tree *t, const dot_rays *rays, const dot_rende
     io.signal = rp.signal_mode != DOT_SIGNAL_NONE ? signal : nullptr;
     io.status = t->status;
     io.grad_vec = ((reinterpret_cast<uintptr_t>(grad_sh) & 15u) == 0) ? 1 : 0;
+    io.touched = touched;
     if (R == 0) return DOT_OK;
     API_CK(dot::launch_march_bwd(t->a.storage, t->a.sh_degree, exact, view_of(t), rs, rp, io, S(stream)),
            "dot_render_backward");
@@ -723,5 +731,48 @@ extern "C" int dot_tree_canonicalize(dot_tree *t, int32_t *leaf_perm, const dot_
     API_CK(e, "dot_tree_canonicalize");
     dot::free_tree_arrays(t->a, t->alloc, S(stream));
     t->a = nw;
+    return DOT_OK;
+}
+
+namespace {
+int check_rms_opts(const dot_rmsprop_opts *opts) {
+    if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
+    if (!(opts->rho >= 0.f && opts->rho < 1.f)) return fail(DOT_ERR_INVALID_ARG, "rho must be in [0, 1)");
+    if (!(opts->eps >= 0.f) || !std::isfinite(opts->lr_sigma) || !std::isfinite(opts->lr_sh))
+        return fail(DOT_ERR_INVALID_ARG, "eps must be >= 0 and learning rates finite");
+    return DOT_OK;
+}
+}  // namespace
+
+extern "C" int dot_rmsprop_step_sparse(dot_tree *t, float *grad_sigma, float *grad_sh,
+                                       float *ms_sigma, float *ms_sh, uint8_t *touched,
+                                       int32_t *last_step, int32_t step, int32_t *work,
+                                       const dot_rmsprop_opts *opts, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if ((rc = check_rms_opts(opts))) return rc;
+    if ((rc = check_uncompressed(t, "dot_rmsprop_step_sparse"))) return rc;
+    if (t->a.n_leaves == 0) return DOT_OK;
+    if (!grad_sigma || !grad_sh || !ms_sigma || !ms_sh || !touched || !last_step || !work)
+        return fail(DOT_ERR_INVALID_ARG, "gradients, mean squares, touched, last_step and work are required");
+    if (step < 1) return fail(DOT_ERR_INVALID_ARG, "step must be >= 1");
+    API_CK(dot::launch_rmsprop_sparse(t->a.storage, t->a.sigma, t->a.sh, t->a.n_leaves, t->a.K,
+                                      t->a.row_stride, grad_sigma, grad_sh, ms_sigma, ms_sh,
+                                      touched, last_step, step, work, *opts, S(stream)),
+           "dot_rmsprop_step_sparse");
+    return DOT_OK;
+}
+
+extern "C" int dot_rmsprop_flush(dot_tree *t, float *ms_sigma, float *ms_sh, int32_t *last_step,
+                                 int32_t step, const dot_rmsprop_opts *opts, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if ((rc = check_rms_opts(opts))) return rc;
+    if (t->a.n_leaves == 0) return DOT_OK;
+    if (!ms_sigma || !ms_sh || !last_step)
+        return fail(DOT_ERR_INVALID_ARG, "mean squares and last_step are required");
+    API_CK(dot::launch_rmsprop_flush(t->a.n_leaves, t->a.K, ms_sigma, ms_sh, last_step, step,
+                                     opts->rho, S(stream)),
+           "dot_rmsprop_flush");
     return DOT_OK;
 }

@@ -62,6 +62,7 @@ struct RenderIO {
     unsigned long long *stats; // STATS [4]
     uint32_t *status;          // device status word
     int32_t grad_vec;          // BWD: grad_sh rows may use 16-byte vector atomics
+    uint8_t *touched;          // BWD: [L] or null; set to 1 for every leaf given a gradient
 };
 
 enum MarchMode : int { kFwd = 0, kBwd = 1, kSignal = 2, kStats = 3 };

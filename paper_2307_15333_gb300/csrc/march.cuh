@@ -143,7 +143,10 @@ template <> __device__ __forceinline__ FF pzero<FF>() { return FF{0.f, 0.f}; }
 struct RayAxes {
     float on[3], dn[3];      // normalised origin and direction (root = [0,1]^3)
     int sg[3];               // direction signs
-    float inv[3], c[3];      // fast mode
+    // fast mode on the 2^16 grid: t(g) = g inv16 + c16 (inv16 = 0, c16 = +inf for a zero
+    // direction, so that axis never exits; inv16 > 0 when the exit face is the upper one); grid
+    // position at t: t dn16 + on16
+    float inv16[3], c16[3], on16[3], dn16[3];
     float ow[3], dw[3], invw[3], lo[3], size;  // exact mode
 };
 
@@ -151,7 +154,7 @@ template <bool EXACT>
 __device__ __forceinline__ typename std::conditional<EXACT, FF, float>::type
 plane_t(const RayAxes &r, int a, float x) {
     if constexpr (!EXACT) {
-        return fmaf(x, r.inv[a], r.c[a]);
+        return fmaf(x * 65536.f, r.inv16[a], r.c16[a]);  // = x inv + c exactly (power-of-2 scaling)
     } else {
         const float p = x * r.size;
         const float pe = fmaf(x, r.size, -p);            // x size = p + pe exactly
@@ -199,8 +202,12 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         r.dn[a] = dw[a] * tv.scale;
         r.sg[a] = r.dn[a] > 0.f ? 1 : (r.dn[a] < 0.f ? -1 : 0);
         if constexpr (!EXACT) {
-            r.inv[a] = 1.f / r.dn[a];
-            r.c[a] = -r.on[a] * r.inv[a];
+            const float inv = 1.f / r.dn[a];
+            // scaling by powers of two is exact: plane times equal x inv + c to the bit
+            r.inv16[a] = r.sg[a] != 0 ? inv * (1.f / 65536.f) : 0.f;
+            r.c16[a] = r.sg[a] != 0 ? -r.on[a] * inv : pinf<float>();
+            r.on16[a] = r.on[a] * 65536.f;
+            r.dn16[a] = r.dn[a] * 65536.f;
         } else {
             r.ow[a] = ow[a];
             r.dw[a] = dw[a];
@@ -264,9 +271,10 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     // descend from (node, level) to the leaf holding gc, recording the path on the stack
     auto descend = [&](int32_t node, int level, int32_t &leaf_out, int &level_out) -> bool {
         int32_t c;
+        const int g0 = gc[0] << 2, g1 = gc[1] << 1, g2 = gc[2];  // slot bits land at 4, 2, 1
         while (true) {
             const int sh = kGridBits - 1 - level;
-            const int j = (((gc[0] >> sh) & 1) << 2) | (((gc[1] >> sh) & 1) << 1) | ((gc[2] >> sh) & 1);
+            const int j = ((g0 >> sh) & 4) | ((g1 >> sh) & 2) | ((g2 >> sh) & 1);
             stack[level * NT] = node;
             c = __ldg(tv.child + (int64_t)node * 8 + j);
             ++level;
@@ -302,6 +310,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
                     dz[ch] = g[ch] * w * ag;
                 }
                 atomicAdd(io.grad_sigma + lf, delta * acc);
+                if (io.touched) io.touched[lf] = 1;
                 float *gr = io.grad_sh + (int64_t)lf * (3 * K);
                 if constexpr ((3 * K) % 4 == 0) {
                     if (io.grad_vec) {
@@ -361,32 +370,56 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         int lo_g[3];
         PT te[3];
         PT tout = pinf<PT>();
+        bool outside = false;
+        if constexpr (!EXACT) {
+            // exit: the nearest of the three faces ahead (a zero direction gives +inf)
+            const int msk = ~(cs - 1);
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            lo_g[a] = gc[a] & ~(cs - 1);
-            if (r.sg[a] != 0) {
-                const int f = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a];
-                te[a] = plane_t<EXACT>(r, a, (float)f * (1.f / 65536.f));
-                if (lt(te[a], tout)) tout = te[a];
-            } else {
-                te[a] = pinf<PT>();
+            for (int a = 0; a < 3; a++) {
+                lo_g[a] = gc[a] & msk;
+                te[a] = fmaf((float)(r.inv16[a] > 0.f ? lo_g[a] + cs : lo_g[a]), r.inv16[a], r.c16[a]);
+            }
+            tout = fminf(fminf(te[0], te[1]), te[2]);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                lo_g[a] = gc[a] & ~(cs - 1);
+                if (r.sg[a] != 0) {
+                    const int f = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a];
+                    te[a] = plane_t<EXACT>(r, a, (float)f * (1.f / 65536.f));
+                    if (lt(te[a], tout)) tout = te[a];
+                } else {
+                    te[a] = pinf<PT>();
+                }
             }
         }
         if (!(val(tout) < pinf<float>())) break;  // only for a zero direction
         const float delta = diff(tout, t);
 
         // ---- next cell and its leaf ----
-        bool outside = false;
         const float toutv = val(tout);
+        if constexpr (!EXACT) {
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (r.sg[a] != 0 && eq(te[a], tout)) {
-                gc[a] = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a] - 1;
-                outside |= (gc[a] < 0) | (gc[a] > 65535);
-            } else {
-                const float p = fmaf(toutv, r.dn[a], r.on[a]);
-                const int gi = (int)floorf(p * 65536.f);
-                gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
+            for (int a = 0; a < 3; a++) {
+                if (te[a] == tout) {  // step across every face hit at tout
+                    gc[a] = r.inv16[a] > 0.f ? lo_g[a] + cs : lo_g[a] - 1;
+                    outside |= (unsigned)gc[a] > 65535u;
+                } else {              // the exit point, clamped into the old cell
+                    const int gi = (int)floorf(fmaf(toutv, r.dn16[a], r.on16[a]));
+                    gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (r.sg[a] != 0 && eq(te[a], tout)) {
+                    gc[a] = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a] - 1;
+                    outside |= (gc[a] < 0) | (gc[a] > 65535);
+                } else {
+                    const float p = fmaf(toutv, r.dn[a], r.on[a]);
+                    const int gi = (int)floorf(p * 65536.f);
+                    gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
+                }
             }
         }
         int32_t next_leaf = 0;

@@ -188,7 +188,181 @@ cudaError_t rmsprop_s(void *sigma, void *sh, int64_t L, int K, int row_stride, f
     return rmsprop_array<S>(reinterpret_cast<S *>(sh), row_stride, grad_sh, ms_sh, L, 3 * K, o, s);
 }
 
+// ---- sparse RMSProp: only the leaves touched since the last step, with deferred decay ----------
+
+// list[count++] = v for every touched leaf (order irrelevant: leaves update independently)
+__global__ void __launch_bounds__(kTrainThreads)
+compact_touched_kernel(const uint8_t *__restrict__ touched, int64_t L, int32_t *__restrict__ list,
+                       int32_t *__restrict__ count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < L; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const bool f = v < L && touched[v] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        int32_t pos = 0;
+        if (lane == 0 && m) pos = atomicAdd(count, __popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (f) list[pos + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+}
+
+// rho^k by binary powering in FP32 (k >= 0)
+__device__ __forceinline__ float rho_pow(float rho, int k) {
+    float r = 1.f, b = rho;
+    while (k > 0) {
+        if (k & 1) r *= b;
+        b *= b;
+        k >>= 1;
+    }
+    return r;
+}
+
+// 16 lanes per touched leaf: lane 0 updates the density, the lanes walk the coefficient row four
+// at a time (16-byte gradient and mean-square loads, coalesced across the lanes)
+template <typename S, bool VEC>
+__global__ void __launch_bounds__(kTrainThreads)
+rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+                      S *__restrict__ sigma, S *__restrict__ sh, int row_stride, int width,
+                      float *__restrict__ grad_sigma, float *__restrict__ grad_sh,
+                      float *__restrict__ ms_sigma, float *__restrict__ ms_sh,
+                      uint8_t *__restrict__ touched, int32_t *__restrict__ last, int32_t step,
+                      float lr_sigma, float lr_sh, Rms o) {
+    const int64_t n = *count;
+    const int gl = threadIdx.x & 15;
+    const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> 4;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4; i < n; i += groups) {
+        const int64_t v = list[i];
+        const float decay = rho_pow(o.rho, step - last[v] - 1);  // the steps it sat out
+        if (gl == 0) {
+            o.lr = lr_sigma;
+            float m = decay * ms_sigma[v];
+            const float p = rms_update(Storage<S>::to_f32(sigma[v]), grad_sigma[v], m, o);
+            ms_sigma[v] = m;
+            sigma[v] = Storage<S>::from_f32(p);
+            if (o.zero_grad) grad_sigma[v] = 0.f;
+        }
+        o.lr = lr_sh;
+        if constexpr (VEC) {
+            using V = Vec4<S>;
+            const int q4 = width / 4;
+            float4 *g4 = reinterpret_cast<float4 *>(grad_sh + v * width);
+            float4 *m4 = reinterpret_cast<float4 *>(ms_sh + v * width);
+            for (int q = gl; q < q4; q += 16) {
+                typename V::T *pv = reinterpret_cast<typename V::T *>(sh + v * row_stride + 4 * q);
+                const float4 g = g4[q];
+                float4 m = m4[q];
+                m.x *= decay;
+                m.y *= decay;
+                m.z *= decay;
+                m.w *= decay;
+                float p[4];
+                V::get(*pv, p);
+                p[0] = rms_update(p[0], g.x, m.x, o);
+                p[1] = rms_update(p[1], g.y, m.y, o);
+                p[2] = rms_update(p[2], g.z, m.z, o);
+                p[3] = rms_update(p[3], g.w, m.w, o);
+                m4[q] = m;
+                *pv = V::make(p);
+                if (o.zero_grad) g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int c = gl; c < width; c += 16) {
+                float *g = grad_sh + v * width + c;
+                float *ms = ms_sh + v * width + c;
+                S *pp = sh + v * row_stride + c;
+                float m = decay * *ms;
+                const float p = rms_update(Storage<S>::to_f32(*pp), *g, m, o);
+                *ms = m;
+                *pp = Storage<S>::from_f32(p);
+                if (o.zero_grad) *g = 0.f;
+            }
+        }
+        __syncwarp(gmask);  // every lane has read last[v]
+        if (gl == 0) {
+            touched[v] = 0;
+            last[v] = step;
+        }
+    }
+}
+
+// ms <- rho^(step - last) ms over the flat [L][width] array (one entry per thread, coalesced);
+// last is only read here and advanced by rmsprop_flush_last_kernel afterwards
+__global__ void __launch_bounds__(kTrainThreads)
+rmsprop_flush_kernel(int64_t L, int width, float *__restrict__ ms_sigma, float *__restrict__ ms_sh,
+                     const int32_t *__restrict__ last, int32_t step, float rho) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n = L * width;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + L; i += stride) {
+        const int64_t v = i < n ? i / width : i - n;
+        const int k = step - last[v];
+        if (k <= 0) continue;
+        const float d = rho_pow(rho, k);
+        if (i < n) ms_sh[i] *= d;
+        else ms_sigma[v] *= d;
+    }
+}
+
+__global__ void __launch_bounds__(kTrainThreads)
+rmsprop_flush_last_kernel(int64_t L, int32_t *__restrict__ last, int32_t step) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L; v += stride)
+        last[v] = step;
+}
+
 }  // namespace
+
+cudaError_t launch_rmsprop_sparse(int storage, void *sigma, void *sh, int64_t L, int K,
+                                  int row_stride, float *grad_sigma, float *grad_sh,
+                                  float *ms_sigma, float *ms_sh, uint8_t *touched, int32_t *last,
+                                  int32_t step, int32_t *work, const dot_rmsprop_opts &op,
+                                  cudaStream_t s) {
+    if (L == 0) return cudaSuccess;
+    int32_t *count = work + L;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    compact_touched_kernel<<<grid_for(L), kTrainThreads, 0, s>>>(touched, L, work, count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Rms o;
+    o.rho = op.rho;
+    o.one_minus_rho = 1.f - op.rho;
+    o.eps = op.eps;
+    o.zero_grad = op.zero_grad;
+    o.lr = 0.f;
+    const int width = 3 * K;
+    const bool vec = width % 4 == 0 && row_stride % 4 == 0 &&
+                     (reinterpret_cast<uintptr_t>(grad_sh) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(ms_sh) & 15) == 0;
+    const int grid = grid_for(L * 16);
+#define DOT_SPARSE_LAUNCH(T)                                                                     \
+    if (vec)                                                                                     \
+        rmsprop_sparse_kernel<T, true><<<grid, kTrainThreads, 0, s>>>(                           \
+            work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh, ms_sigma,  \
+            ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);                               \
+    else                                                                                         \
+        rmsprop_sparse_kernel<T, false><<<grid, kTrainThreads, 0, s>>>(                          \
+            work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh, ms_sigma,  \
+            ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);
+    switch (storage) {
+        case DOT_STORAGE_F32: DOT_SPARSE_LAUNCH(float) break;
+        case DOT_STORAGE_F16: DOT_SPARSE_LAUNCH(__half) break;
+        default: DOT_SPARSE_LAUNCH(__nv_bfloat16) break;
+    }
+#undef DOT_SPARSE_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmsprop_flush(int64_t L, int K, float *ms_sigma, float *ms_sh, int32_t *last,
+                                 int32_t step, float rho, cudaStream_t s) {
+    if (L == 0) return cudaSuccess;
+    rmsprop_flush_kernel<<<grid_for(L * (3 * K + 1)), kTrainThreads, 0, s>>>(L, 3 * K, ms_sigma,
+                                                                             ms_sh, last, step, rho);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rmsprop_flush_last_kernel<<<grid_for(L), kTrainThreads, 0, s>>>(L, last, step);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mse_grad(const float *rgb, const float *target, int64_t n_rays, float *grad,
                             double *loss_sum, cudaStream_t s) {

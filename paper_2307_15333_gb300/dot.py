@@ -39,7 +39,8 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_render_forward", "dot_render_backward", "dot_accumulate_signal",
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
-                "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize")
+                "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize",
+                "dot_rmsprop_step_sparse", "dot_rmsprop_flush")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -162,7 +163,7 @@ def lib() -> ctypes.CDLL:
         "dot_tree_import": [ctypes.POINTER(dot_host_tree), ctypes.POINTER(dot_allocator), P, ctypes.POINTER(P)],
         "dot_tree_status": [P, P, ctypes.POINTER(ctypes.c_uint32)],
         "dot_render_forward": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), P, P, P, P],
-        "dot_render_backward": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), P, P, P, P, P, P],
+        "dot_render_backward": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), P, P, P, P, P, P, P],
         "dot_accumulate_signal": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts), ctypes.c_int32, P, P],
         "dot_select_masks": [P, P, ctypes.POINTER(dot_select_opts), P, P, P],
         "dot_refine_plan": [P, P, P, ctypes.c_int32, ctypes.POINTER(dot_refine_counts), P],
@@ -174,6 +175,8 @@ def lib() -> ctypes.CDLL:
         "dot_rmsprop_step": [P, P, P, P, P, ctypes.POINTER(dot_rmsprop_opts), P],
         "dot_compress_sh": [P, ctypes.c_int32, P],
         "dot_tree_canonicalize": [P, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
+        "dot_rmsprop_step_sparse": [P, P, P, P, P, P, P, ctypes.c_int32, P, ctypes.POINTER(dot_rmsprop_opts), P],
+        "dot_rmsprop_flush": [P, P, P, P, ctypes.c_int32, ctypes.POINTER(dot_rmsprop_opts), P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -472,7 +475,8 @@ def dot_render_forward(tree: Octree, rays: dot_rays, opts: dot_render_opts, rgb:
 
 def dot_render_backward(tree: Octree, rays: dot_rays, opts: dot_render_opts,
                         grad_rgb: torch.Tensor, rgb: torch.Tensor, grad_sigma: torch.Tensor,
-                        grad_sh: torch.Tensor, signal: Optional[torch.Tensor] = None, stream=None):
+                        grad_sh: torch.Tensor, signal: Optional[torch.Tensor] = None,
+                        touched: Optional[torch.Tensor] = None, stream=None):
     R = n_rays_of(rays)
     inf = tree.info()
     _need(grad_rgb, torch.float32, 3 * R, "grad_rgb")
@@ -481,9 +485,11 @@ def dot_render_backward(tree: Octree, rays: dot_rays, opts: dot_render_opts,
     _need(grad_sh, torch.float32, inf.n_leaves * 3 * inf.n_coeffs, "grad_sh")
     if signal is not None:
         _need(signal, torch.float32, inf.n_leaves, "signal")
+    if touched is not None:
+        _need(touched, torch.uint8, inf.n_leaves, "touched")
     _check(lib().dot_render_backward(tree.handle, ctypes.byref(rays), ctypes.byref(opts),
                                      _ptr(grad_rgb), _ptr(rgb), _ptr(grad_sigma), _ptr(grad_sh),
-                                     _ptr(signal), _stream(stream)))
+                                     _ptr(signal), _ptr(touched), _stream(stream)))
 
 
 def dot_accumulate_signal(tree: Octree, rays: Optional[dot_rays], opts: dot_render_opts,
@@ -597,6 +603,36 @@ def dot_rmsprop_step(tree: Octree, grad_sigma: torch.Tensor, grad_sh: torch.Tens
     _need(ms_sh, torch.float32, L * 3 * K, "ms_sh")
     _check(lib().dot_rmsprop_step(tree.handle, _ptr(grad_sigma), _ptr(grad_sh), _ptr(ms_sigma),
                                   _ptr(ms_sh), ctypes.byref(opts), _stream(stream)))
+
+
+def dot_rmsprop_step_sparse(tree: Octree, grad_sigma, grad_sh, ms_sigma, ms_sh,
+                            touched: torch.Tensor, last_step: torch.Tensor, step: int,
+                            work: torch.Tensor, opts: dot_rmsprop_opts, stream=None):
+    """RMSProp of the touched leaves only, the decay of the others deferred (see dot.h)."""
+    inf = tree.info()
+    L, K = inf.n_leaves, inf.n_coeffs
+    _need(grad_sigma, torch.float32, L, "grad_sigma")
+    _need(ms_sigma, torch.float32, L, "ms_sigma")
+    _need(grad_sh, torch.float32, L * 3 * K, "grad_sh")
+    _need(ms_sh, torch.float32, L * 3 * K, "ms_sh")
+    _need(touched, torch.uint8, L, "touched")
+    _need(last_step, torch.int32, L, "last_step")
+    _need(work, torch.int32, L + 1, "work")
+    _check(lib().dot_rmsprop_step_sparse(tree.handle, _ptr(grad_sigma), _ptr(grad_sh),
+                                         _ptr(ms_sigma), _ptr(ms_sh), _ptr(touched),
+                                         _ptr(last_step), int(step), _ptr(work),
+                                         ctypes.byref(opts), _stream(stream)))
+
+
+def dot_rmsprop_flush(tree: Octree, ms_sigma, ms_sh, last_step: torch.Tensor, step: int,
+                      opts: dot_rmsprop_opts, stream=None):
+    inf = tree.info()
+    L, K = inf.n_leaves, inf.n_coeffs
+    _need(ms_sigma, torch.float32, L, "ms_sigma")
+    _need(ms_sh, torch.float32, L * 3 * K, "ms_sh")
+    _need(last_step, torch.int32, L, "last_step")
+    _check(lib().dot_rmsprop_flush(tree.handle, _ptr(ms_sigma), _ptr(ms_sh), _ptr(last_step),
+                                   int(step), ctypes.byref(opts), _stream(stream)))
 
 
 def dot_compress_sh(tree: Octree, bits: int, stream=None):

@@ -3,8 +3,10 @@
 One optimisation step on a batch of stochastic ray samples (Sec. 4.1):
     forward render with the training signal fused (Sec. 3.1: Q accumulates over the epoch),
     MSE loss and dL/dC (dot_mse_grad), backward march into FP32 gradients
-    (dot_render_backward), RMSProp update of every leaf fused with zeroing the gradients
-    (dot_rmsprop_step; Sec. 3.3, learning rates of Sec. 4.1).
+    (dot_render_backward, which also flags the leaves it touches), RMSProp update fused with
+    zeroing the gradients (Sec. 3.3, learning rates of Sec. 4.1): by default only over the touched
+    leaves, with the pure decay of the others deferred (dot_rmsprop_step_sparse, the same update
+    up to FP32 rounding), else over every leaf (dot_rmsprop_step).
 Every T epochs (Algorithm 1) the tree is refined from the accumulated signal: pruning with
 threshold tau (optionally recursive, merging parents upward while groups still qualify, the
 merged signal being the sum -- or max -- of the children's), then sampling of the top-gamma
@@ -26,8 +28,10 @@ from . import dot
 class Trainer:
     def __init__(self, tree: dot.Octree, opts: dot.dot_render_opts,
                  rms: Optional[dot.dot_rmsprop_opts] = None,
-                 signal_mode: int = dot.DOT_SIGNAL_SUM_ALPHA, stream=None):
+                 signal_mode: int = dot.DOT_SIGNAL_SUM_ALPHA, stream=None, sparse: bool = True):
         self.tree = tree
+        self.sparse = sparse
+        self.step_no = 0
         self.opts = dot.render_opts(background=tuple(opts.background), eps_T=opts.eps_T,
                                     color_act=opts.color_act, signal_mode=signal_mode,
                                     precision=opts.precision, max_steps=opts.max_steps)
@@ -49,6 +53,13 @@ class Trainer:
         if zero_ms:
             self.ms_sigma = torch.zeros(L, dtype=torch.float32, device="cuda")
             self.ms_sh = torch.zeros(L, 3, K, dtype=torch.float32, device="cuda")
+        self._alloc_sparse_state()
+
+    def _alloc_sparse_state(self):
+        L = self.L
+        self.touched = torch.zeros(L, dtype=torch.uint8, device="cuda")
+        self.last_step = torch.full((L,), self.step_no, dtype=torch.int32, device="cuda")
+        self.work = torch.empty(L + 1, dtype=torch.int32, device="cuda")
 
     def _buffers(self, R: int):
         if self._batch != R:
@@ -70,9 +81,22 @@ class Trainer:
                                 color_act=self.opts.color_act, precision=self.opts.precision,
                                 max_steps=self.opts.max_steps)
         dot.dot_render_backward(self.tree, rays, plain, self.grad_rgb, self.rgb,
-                                self.grad_sigma, self.grad_sh, stream=s)
-        dot.dot_rmsprop_step(self.tree, self.grad_sigma, self.grad_sh, self.ms_sigma,
-                             self.ms_sh, self.rms, stream=s)
+                                self.grad_sigma, self.grad_sh,
+                                touched=self.touched if self.sparse else None, stream=s)
+        self.step_no += 1
+        if self.sparse:
+            dot.dot_rmsprop_step_sparse(self.tree, self.grad_sigma, self.grad_sh, self.ms_sigma,
+                                        self.ms_sh, self.touched, self.last_step, self.step_no,
+                                        self.work, self.rms, stream=s)
+        else:
+            dot.dot_rmsprop_step(self.tree, self.grad_sigma, self.grad_sh, self.ms_sigma,
+                                 self.ms_sh, self.rms, stream=s)
+
+    def flush(self):
+        """Brings every leaf's RMSProp mean squares up to the current step (sparse mode)."""
+        if self.sparse:
+            dot.dot_rmsprop_flush(self.tree, self.ms_sigma, self.ms_sh, self.last_step,
+                                  self.step_no, self.rms, stream=self.stream)
 
     # ---- Algorithm 1, pruning and sampling -------------------------------------------------
     def refine(self, tau: float, gamma: float, depth_cap: int, recursive: bool = False,
@@ -82,6 +106,7 @@ class Trainer:
         fraction by the signal (Algorithm 1); with `canonical` the tree is then renumbered in
         breadth-first Morton order (the RMSProp state follows).  Returns the plan of each pass."""
         merge = dot.DOT_MERGE_MAX if self.signal_mode == dot.DOT_SIGNAL_MAX_WEIGHT else dot.DOT_MERGE_SUM
+        self.flush()
         passes = []
         while True:
             pm, sm = self._marks(dot.select_opts(prune_mode, tau, dot.DOT_SELECT_NONE, 0.0))
@@ -108,6 +133,7 @@ class Trainer:
         self.grad_sigma = torch.zeros(self.L, dtype=torch.float32, device="cuda")
         self.grad_sh = torch.zeros(self.L, 3, self.K, dtype=torch.float32, device="cuda")
         self.signal = torch.zeros(self.L, dtype=torch.float32, device="cuda")
+        self._alloc_sparse_state()
         return {"passes": passes, "n_leaves": self.L, "n_nodes": self.tree.n_nodes}
 
     def _marks(self, sel: dot.dot_select_opts):

@@ -116,3 +116,37 @@ def test_accumulate_signal(mode):
             dot.dot_render_forward(tree, _rays(o, d), dot.render_opts(signal_mode=m), rgb, None, sig2)
             torch.testing.assert_close(sig2, sig, rtol=1e-6, atol=1e-6)
     tree.free()
+
+
+def test_large_backward_launch_equals_small_launches():
+    """A backward over 400 k camera rays (the occupancy build for launches of two full waves)
+    gives the gradients of the same rays run as small buffer launches (the build the oracle
+    parity tests cover), up to the order of the FP32 atomic sums."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(44, max_depth=6, sh_degree=3, storage=si.STORAGE_F16, n_prims=4)
+    tree = dot.octree_from_scene(scene)
+    cams = [si.pinhole((0.2, 0.9, 2.8), 640, 640, 700.0)]
+    R = 640 * 640
+    opts = dot.render_opts(background=(1, 1, 1), eps_T=1e-4)
+    rays = dot.rays_cameras(dot.cameras_tensor(cams), 640, 640)
+    rgb = torch.empty(R, 3, device="cuda")
+    dot.dot_render_forward(tree, rays, opts, rgb)
+    g = torch.from_numpy(np.random.default_rng(4).normal(0, 1e-2, (R, 3)).astype(np.float32)).cuda()
+    L, K = tree.n_leaves, 16
+    gs_a, gsh_a = torch.zeros(L, device="cuda"), torch.zeros(L, 3, K, device="cuda")
+    dot.dot_render_backward(tree, rays, opts, g, rgb, gs_a, gsh_a)
+    o, d = si.camera_rays(cams[0])
+    gs_b, gsh_b = torch.zeros(L, device="cuda"), torch.zeros(L, 3, K, device="cuda")
+    step = 100_000                      # below the two-wave threshold: the small-launch build
+    for s in range(0, R, step):
+        e = min(R, s + step)
+        rb = dot.rays_buffer(torch.from_numpy(o[s:e]).cuda(), torch.from_numpy(d[s:e]).cuda())
+        dot.dot_render_backward(tree, rb, opts, g[s:e].contiguous(), rgb[s:e].contiguous(), gs_b, gsh_b)
+    torch.cuda.synchronize()
+    for a, b in ((gs_a, gs_b), (gsh_a, gsh_b)):
+        a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        scale = np.abs(a).max()
+        assert scale > 0
+        assert np.abs(a - b).max() <= 1e-5 * scale + 1e-9
+    assert tree.status() == 0
+    tree.free()

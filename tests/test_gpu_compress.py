@@ -115,3 +115,38 @@ def test_compressed_tree_refuses_training_and_refine():
     assert e.value.code == dot.dot.DOT_ERR_UNSUPPORTED
     tree.free()
     f32.free()
+
+
+def test_slot_tables_serve_compressed_trees():
+    """Requests on compressed trees through one slot-table launch equal plain forward renders,
+    and a table mixing compressed and uncompressed trees is refused."""
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300 import serve
+    trees = [dot.octree_from_scene(si.random_scene(97 + i, max_depth=5, sh_degree=3,
+                                                   storage=si.STORAGE_F16, n_prims=3))
+             for i in range(2)]
+    for t in trees:
+        dot.dot.dot_compress_sh(t, 8)
+    opts = dot.render_opts(background=(1, 1, 1), eps_T=1e-4)
+    rng = np.random.default_rng(0)
+    reqs = []
+    for i, (w, h) in enumerate([(64, 48), (200, 120), (33, 77)]):
+        pos = 3.0 * np.array([rng.uniform(-1, 1), rng.uniform(0.2, 1), rng.uniform(-1, 1)])
+        reqs.append(serve.Request(i, i % 2, w, h, si.pinhole(pos, w, h, 1.2 * w).packed(), 0.0))
+    srv = serve.BatchedServer(trees, opts, pool_floats=4 << 20, max_slots=8)
+    mixed, alone = srv.render_alone_and_mixed(reqs)
+    for r, m, a in zip(reqs, mixed, alone):
+        assert torch.equal(m, a)
+        ref = torch.empty(r.width * r.height, 3, device="cuda")
+        cam = torch.from_numpy(r.camera).cuda().view(1, 18)
+        dot.dot_render_forward(trees[r.tree], dot.rays_cameras(cam, r.width, r.height), opts, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(m.view(-1, 3), ref)
+    plain = dot.octree_from_scene(si.random_scene(99, max_depth=4, sh_degree=3,
+                                                  storage=si.STORAGE_F16, n_prims=2))
+    table = torch.zeros(16 + 96 * 4, dtype=torch.uint8, device="cuda")
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(dot.DotError):
+        dot.dot.dot_render_slots([trees[0], plain], table, 4, opts, counter)
+    for t in trees + [plain]:
+        t.free()

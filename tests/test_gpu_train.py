@@ -114,6 +114,7 @@ def test_training_loop_matches_oracle():
         h64, ms_h = oracle.rmsprop(h64, ms_h, gsh, lr_h, rho, eps)
         s64 = s64.astype(np.float32).astype(np.float64)
         h64 = h64.astype(np.float32).astype(np.float64)
+    tr.flush()
     torch.cuda.synchronize()
     assert tree.status() == 0
     got_s = tree.sigma.cpu().numpy().astype(np.float64)
@@ -155,4 +156,57 @@ def test_training_loop_matches_oracle():
     ms3 = oracle.remap_leaf_values(nt, lm3, ms_s2, "mean")
     np.testing.assert_allclose(tr.ms_sigma.cpu().numpy(), ms3, rtol=1e-3, atol=1e-9)
     assert tr.L == nt3["leaf_key"].size and tr.grad_sigma.shape[0] == tr.L
+    tree.free()
+
+
+@pytest.mark.parametrize("storage", [si.STORAGE_F32, si.STORAGE_F16, si.STORAGE_BF16])
+def test_sparse_rmsprop_equals_dense(storage):
+    """Six steps in which a random fifth of the leaves have gradients: the sparse update (touched
+    leaves only, deferred decay, final flush) against the oracle's dense RMSProp of every leaf."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(61, max_depth=5, sh_degree=3, storage=storage, n_prims=3)
+    tree = dot.octree_from_scene(scene)
+    L, K = tree.n_leaves, 16
+    rng = np.random.default_rng(storage)
+    p_s = tree.sigma.float().cpu().numpy().astype(np.float64)
+    p_h = tree.sh.float().cpu().numpy().astype(np.float64)
+    ms_s, ms_h = np.zeros(L), np.zeros((L, 3, K))
+    t_gs = torch.zeros(L, device="cuda")
+    t_gsh = torch.zeros(L, 3, K, device="cuda")
+    t_ms, t_msh = torch.zeros(L, device="cuda"), torch.zeros(L, 3, K, device="cuda")
+    touched = torch.zeros(L, dtype=torch.uint8, device="cuda")
+    last = torch.zeros(L, dtype=torch.int32, device="cuda")
+    work = torch.empty(L + 1, dtype=torch.int32, device="cuda")
+    opts = dot.dot.rmsprop_opts(lr_sigma=0.1, lr_sh=0.01, rho=0.9, eps=1e-8)
+    moved_s, moved_h = np.zeros(L), np.zeros((L, 3, K))     # sum of |update| per entry
+    for step in range(1, 7):
+        hit = rng.random(L) < 0.2
+        gs = np.where(hit, rng.normal(size=L) * 0.1, 0.0).astype(np.float32)
+        gsh = np.where(hit[:, None, None], rng.normal(size=(L, 3, K)) * 0.01, 0.0).astype(np.float32)
+        t_gs.copy_(torch.from_numpy(gs))
+        t_gsh.copy_(torch.from_numpy(gsh))
+        touched.copy_(torch.from_numpy(hit.astype(np.uint8)))
+        dot.dot.dot_rmsprop_step_sparse(tree, t_gs, t_gsh, t_ms, t_msh, touched, last, step, work, opts)
+        q_s, ms_s = oracle.rmsprop(p_s, ms_s, gs, 0.1, 0.9, 1e-8)
+        q_h, ms_h = oracle.rmsprop(p_h, ms_h, gsh, 0.01, 0.9, 1e-8)
+        moved_s += np.abs(q_s - p_s)
+        moved_h += np.abs(q_h - p_h)
+        p_s, p_h = q_s, q_h
+        # the stored parameters are what the next step reads
+        p_s = si.storage_to_f64(si.round_to_storage(p_s.astype(np.float32), storage), storage)
+        p_h = si.storage_to_f64(si.round_to_storage(p_h.astype(np.float32), storage), storage)
+        torch.cuda.synchronize()
+        assert not touched.any() and not t_gs.any() and not t_gsh.any()
+    dot.dot.dot_rmsprop_flush(tree, t_ms, t_msh, last, 6, opts)
+    torch.cuda.synchronize()
+    assert (last.cpu().numpy() == 6).all()
+    np.testing.assert_allclose(t_ms.cpu().numpy(), ms_s, rtol=1e-5, atol=1e-30)
+    np.testing.assert_allclose(t_msh.cpu().numpy(), ms_h, rtol=1e-5, atol=1e-30)
+    # each step rounds to the storage type (one ulp either way near a rounding boundary) after an
+    # FP32 update whose error is ~1e-6 of the magnitudes involved
+    for got, ref, moved in ((tree.sigma, p_s, moved_s), (tree.sh, p_h, moved_h)):
+        got = got.float().cpu().numpy().astype(np.float64)
+        lim = _ulp(ref, storage) + 1e-6 * (np.abs(ref) + moved)
+        d = np.abs(got - ref)
+        assert (d <= lim).mean() > 0.999 and (d <= 3 * lim).all(), f"worst {(d / lim).max():.3g} x limit"
     tree.free()
