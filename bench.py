@@ -529,6 +529,24 @@ def run_dot(args):
                "grad": "fixed synthetic dL/dC; FP32 gradients accumulate across pairs",
                "clocks": clk2}
 
+    # ---- the same batches through the fused training pass (forward, MSE gradient and backward
+    # in one launch; the backward scatters from each ray's recorded segments) ----
+    tgt = torch.full((BATCH, 3), 0.5, dtype=torch.float32, device="cuda")
+    gfused = torch.empty(BATCH, 3, device="cuda")
+    for i in range(3 * nb):
+        dot.dot.dot_render_forward_backward_mse(tree, batches[i % nb], opts, tgt, brgb, gfused, gs, gsh)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(pairs):
+        dot.dot.dot_render_forward_backward_mse(tree, batches[i % nb], opts, tgt, brgb, gfused, gs, gsh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fu_ms = max_over_ranks(e0.elapsed_time(e1))
+    fwd_bwd["fused_mse"] = {"value": BATCH * pairs * ws / (fu_ms / 1e3) / 1e6, "unit": "Mrays/s",
+                            "batch_rays": BATCH, "passes": pairs, "ms_per_pass": fu_ms / pairs,
+                            "pass": "forward + MSE gradient + backward in one launch"}
+    del tgt, gfused
+
     # ---- forward + backward over all views in one batch (64 M rays per pair) ----
     gfull = torch.full((R, 3), 1e-6, dtype=torch.float32, device="cuda")
     for _ in range(2):

@@ -299,6 +299,24 @@ int dot_render_backward(const dot_tree *tree, const dot_rays *rays, const dot_re
                         float *grad_sh, float *signal, uint8_t *touched, void *stream);
 
 /*
+ * dot_render_forward_backward_mse -- one training pass over a batch of rays in one launch: the
+ * forward render (Eq. 1-2, as dot_render_forward, with its fused signal), the MSE gradient
+ * grad_rgb = 2 (rgb - target) / (3R) (as dot_mse_grad; loss_sum += the MSE), and the backward
+ * (as dot_render_backward with that gradient).  Each ray records its occupied segments (weight,
+ * transmittance, length, colour) while marching forward and scatters the gradients from that
+ * record, so the backward takes no second traversal; a ray with more than 32 occupied segments
+ * marches again in the backward mode.  Results equal the three separate calls up to the order
+ * of the FP32 atomic sums.
+ * target, rgb, grad_rgb: device [R][3] float (rgb and grad_rgb written, all distinct);
+ * loss_sum: device double or NULL; grad_sigma [L], grad_sh [L][3][K]: accumulated (+=); signal
+ * and touched as in dot_render_forward / dot_render_backward.  Not for compressed trees.
+ */
+int dot_render_forward_backward_mse(const dot_tree *tree, const dot_rays *rays,
+                                    const dot_render_opts *opts, const float *target, float *rgb,
+                                    float *grad_rgb, double *loss_sum, float *grad_sigma,
+                                    float *grad_sh, float *signal, uint8_t *touched, void *stream);
+
+/*
  * dot_accumulate_signal -- the per-leaf training signal of Sec. 3.1 (Algorithm 1, optimization
  * step): SUM_ALPHA or MAX_WEIGHT by marching the rays (densities only), or SIGMA (no rays).
  * signal: device [L] float, accumulated (SIGMA: written).

@@ -26,6 +26,9 @@ cudaError_t launch_march_bwd(int storage, int deg, bool exact, const TreeView &t
                              cudaStream_t stream);
 cudaError_t launch_march_signal(int storage, bool exact, const TreeView &tv, const RaySource &rs,
                                 const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
+cudaError_t launch_march_fwdbwd(int storage, int deg, bool exact, const TreeView &tv,
+                                const RaySource &rs, const RenderParams &rp, const RenderIO &io,
+                                cudaStream_t stream);
 cudaError_t launch_march_stats(int storage, bool exact, const TreeView &tv, const RaySource &rs,
                                const RenderParams &rp, const RenderIO &io, cudaStream_t stream);
 cudaError_t compress_tree(TreeArrays &a, int bits, const DevAlloc &al, cudaStream_t s);
@@ -774,5 +777,44 @@ extern "C" int dot_rmsprop_flush(dot_tree *t, float *ms_sigma, float *ms_sh, int
     API_CK(dot::launch_rmsprop_flush(t->a.n_leaves, t->a.K, ms_sigma, ms_sh, last_step, step,
                                      opts->rho, S(stream)),
            "dot_rmsprop_flush");
+    return DOT_OK;
+}
+
+extern "C" int dot_render_forward_backward_mse(const dot_tree *t, const dot_rays *rays,
+                                               const dot_render_opts *opts, const float *target,
+                                               float *rgb, float *grad_rgb, double *loss_sum,
+                                               float *grad_sigma, float *grad_sh, float *signal,
+                                               uint8_t *touched, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    if ((rc = check_uncompressed(t, "dot_render_forward_backward_mse"))) return rc;
+    dot::RaySource rs;
+    int64_t R = 0;
+    if ((rc = make_rays(rays, rs, R))) return rc;
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    if (R > 0 && (!target || !rgb || !grad_rgb || !grad_sigma || !grad_sh))
+        return fail(DOT_ERR_INVALID_ARG, "target, rgb, grad_rgb, grad_sigma and grad_sh are required");
+    if (grad_rgb == rgb || grad_rgb == target || rgb == target)
+        return fail(DOT_ERR_INVALID_ARG, "target, rgb and grad_rgb must be distinct buffers");
+    if (rp.signal_mode != DOT_SIGNAL_NONE && !signal)
+        return fail(DOT_ERR_INVALID_ARG, "signal_mode set but signal is NULL");
+    dot::RenderIO io{};
+    io.rgb = rgb;
+    io.target = target;
+    io.grad_out = grad_rgb;
+    io.loss_sum = loss_sum;
+    io.inv3R = R > 0 ? (float)(1.0 / (3.0 * (double)R)) : 0.f;
+    io.grad_sigma = grad_sigma;
+    io.grad_sh = grad_sh;
+    io.signal = rp.signal_mode != DOT_SIGNAL_NONE ? signal : nullptr;
+    io.touched = touched;
+    io.status = t->status;
+    io.grad_vec = ((reinterpret_cast<uintptr_t>(grad_sh) & 15u) == 0) ? 1 : 0;
+    if (R == 0) return DOT_OK;
+    API_CK(dot::launch_march_fwdbwd(t->a.storage, t->a.sh_degree, exact, view_of(t), rs, rp, io,
+                                    S(stream)),
+           "dot_render_forward_backward_mse");
     return DOT_OK;
 }

@@ -63,9 +63,21 @@ struct RenderIO {
     uint32_t *status;          // device status word
     int32_t grad_vec;          // BWD: grad_sh rows may use 16-byte vector atomics
     uint8_t *touched;          // BWD: [L] or null; set to 1 for every leaf given a gradient
+    const float *target;       // FWDBWD [R][3]: MSE target
+    float *grad_out;           // FWDBWD [R][3]: dL/dC written (read back by the overflow re-march)
+    double *loss_sum;          // FWDBWD: += sum (rgb - target)^2 * inv3R (or null)
+    float inv3R;               // FWDBWD: 1 / (3 R)
 };
 
-enum MarchMode : int { kFwd = 0, kBwd = 1, kSignal = 2, kStats = 3 };
+// kFwdBwd: forward, MSE gradient and backward of each ray in one pass -- the occupied segments are
+// recorded during the forward march and the gradients scattered from the record, so the
+// backward needs no second traversal (rays with more occupied segments than the record holds
+// march again in the backward mode).
+enum MarchMode : int { kFwd = 0, kBwd = 1, kSignal = 2, kStats = 3, kFwdBwd = 4 };
+#ifndef DOT_RECORD_SEGMENTS
+#define DOT_RECORD_SEGMENTS 32
+#endif
+constexpr int kRecordSegments = DOT_RECORD_SEGMENTS;
 
 // ---------------------------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)

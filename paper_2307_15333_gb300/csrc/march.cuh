@@ -181,6 +181,9 @@ plane_t(const RayAxes &r, int a, float x) {
 struct RayOut {
     float rgb[3];
     float T;
+    float loss = 0.f;       // FWDBWD: the ray's squared error summed over channels
+    bool overflow = false;  // FWDBWD: more occupied segments than the record holds
+    float g[3], rgbf[3];    // BWD in: dL/dC and the forward colour; FWDBWD out: dL/dC
     unsigned long long st[4];  // STATS: hit, steps, occupied, child loads
 };
 
@@ -238,18 +241,31 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     if (!hit || !lt(tn, tf)) {
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) out.rgb[ch] = rp.bg[ch];
+        if constexpr (MODE == kFwdBwd) {
+            float loss = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                const float e = out.rgb[ch] - __ldg(io.target + 3 * ray + ch);
+                out.g[ch] = 2.f * e * io.inv3R;
+                loss = fmaf(e, e, loss);
+            }
+            out.loss = loss;
+        }
         return;
     }
     if constexpr (MODE == kStats) out.st[0] += 1;
 
+    constexpr bool SHADE = MODE == kFwd || MODE == kBwd || MODE == kFwdBwd;
     float Y[K];
-    if constexpr (MODE == kFwd || MODE == kBwd) sh_basis<K>(dw[0], dw[1], dw[2], Y);
+    if constexpr (SHADE) sh_basis<K>(dw[0], dw[1], dw[2], Y);
+    float4 rec[MODE == kFwdBwd ? 2 * kRecordSegments : 1];  // (leaf, w, Tn, delta), (colour)
+    int nrec = 0;
     float g[3], rgbf[3];
     if constexpr (MODE == kBwd) {
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) {
-            g[ch] = __ldg(io.grad_rgb + 3 * ray + ch);
-            rgbf[ch] = __ldg(io.rgb_fwd + 3 * ray + ch);
+            g[ch] = out.g[ch];
+            rgbf[ch] = out.rgbf[ch];
         }
     }
 
@@ -290,8 +306,48 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     // colour of one occupied segment (weight w, transmittance after it Tn, length delta):
     // C += w c; the backward also scatters dL/dsigma and dL/dSH for it.  Segments are shaded in
     // march order, so C is the prefix sum C_{<=i} the backward needs.
+    // gradient of one occupied segment given C = C_{<=i} (colour up to and including it), the
+    // ray's dL/dC g and its rendered colour rgbf: dL/dsigma and dL/dSH scattered into the leaf
+    auto scatter = [&](int32_t lf, float w, float Tn, float delta, const float col[3]) {
+        float acc = 0.f;
+        float dz[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            const float suffix = rgbf[ch] - C[ch];
+            acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
+            const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
+            dz[ch] = g[ch] * w * ag;
+        }
+        atomicAdd(io.grad_sigma + lf, delta * acc);
+        if (io.touched) io.touched[lf] = 1;
+        float *gr = io.grad_sh + (int64_t)lf * (3 * K);
+        if constexpr ((3 * K) % 4 == 0) {
+            if (io.grad_vec) {
+                float4 *g4 = reinterpret_cast<float4 *>(gr);
+#pragma unroll
+                for (int q = 0; q < 3 * K / 4; q++) {
+                    float4 v;
+                    v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
+                    v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
+                    v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
+                    v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
+                    atomicAdd(g4 + q, v);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
+        }
+    };
+
+    // colour of one occupied segment (weight w, transmittance after it Tn, length delta):
+    // C += w c; the backward also scatters dL/dsigma and dL/dSH for it, the fused mode records
+    // it.  Segments are shaded in march order, so C is the prefix sum C_{<=i} the backward needs.
     auto shade = [&](int32_t lf, int64_t row, float w, float Tn, float delta) {
-        if constexpr (MODE == kFwd || MODE == kBwd) {
+        if constexpr (SHADE) {
             float z[3], col[3];
             leaf_z<S, K>(shp + row * tv.row_stride, Y, z);
 #pragma unroll
@@ -299,39 +355,13 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
                 col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(w, col[ch], C[ch]);
-            if constexpr (MODE == kBwd) {
-                float acc = 0.f;
-                float dz[3];
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++) {
-                    const float suffix = rgbf[ch] - C[ch];
-                    acc = fmaf(g[ch], Tn * col[ch] - suffix, acc);
-                    const float ag = rp.color_act == DOT_ACT_LINEAR ? 1.f : col[ch] * (1.f - col[ch]);
-                    dz[ch] = g[ch] * w * ag;
+            if constexpr (MODE == kBwd) scatter(lf, w, Tn, delta, col);
+            if constexpr (MODE == kFwdBwd) {
+                if (nrec < kRecordSegments) {
+                    rec[2 * nrec] = make_float4(__int_as_float(lf), w, Tn, delta);
+                    rec[2 * nrec + 1] = make_float4(col[0], col[1], col[2], 0.f);
                 }
-                atomicAdd(io.grad_sigma + lf, delta * acc);
-                if (io.touched) io.touched[lf] = 1;
-                float *gr = io.grad_sh + (int64_t)lf * (3 * K);
-                if constexpr ((3 * K) % 4 == 0) {
-                    if (io.grad_vec) {
-                        float4 *g4 = reinterpret_cast<float4 *>(gr);
-#pragma unroll
-                        for (int q = 0; q < 3 * K / 4; q++) {
-                            float4 v;
-                            v.x = dz[(4 * q + 0) / K] * Y[(4 * q + 0) % K];
-                            v.y = dz[(4 * q + 1) / K] * Y[(4 * q + 1) % K];
-                            v.z = dz[(4 * q + 2) / K] * Y[(4 * q + 2) % K];
-                            v.w = dz[(4 * q + 3) / K] * Y[(4 * q + 3) % K];
-                            atomicAdd(g4 + q, v);
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 3 * K; i++) atomicAdd(gr + i, dz[i / K] * Y[i % K]);
-                }
+                ++nrec;
             }
         }
     };
@@ -441,7 +471,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             const float e = ex<EXACT>(-(sv * delta));
             const float alpha = 1.f - e;
             const float w = T * alpha;
-            if constexpr (MODE == kFwd || MODE == kBwd) {
+            if constexpr (SHADE) {
                 if constexpr (DEFER) {
                     prefetch_row<S, K>(shp + row * tv.row_stride);
                     if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
@@ -467,12 +497,38 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         leaf = next_leaf;
         level = next_level;
     }
-    if constexpr (DEFER && (MODE == kFwd || MODE == kBwd)) {
+    if constexpr (DEFER && SHADE) {
         if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) out.rgb[ch] = fmaf(T, rp.bg[ch], C[ch]);
     out.T = T;
+    if constexpr (MODE == kFwdBwd) {
+        // MSE gradient of this ray, then the backward from the record of its occupied segments
+        float loss = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            rgbf[ch] = out.rgb[ch];
+            const float e = rgbf[ch] - __ldg(io.target + 3 * ray + ch);
+            g[ch] = 2.f * e * io.inv3R;
+            loss = fmaf(e, e, loss);
+            out.g[ch] = g[ch];
+        }
+        out.loss = loss;
+        if (nrec <= kRecordSegments) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) C[ch] = 0.f;
+            for (int i = 0; i < nrec; i++) {
+                const float4 a = rec[2 * i], b = rec[2 * i + 1];
+                const float col[3] = {b.x, b.y, b.z};
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(a.y, col[ch], C[ch]);
+                scatter(__float_as_int(a.x), a.y, a.z, a.w, col);
+            }
+        } else {
+            out.overflow = true;  // the caller re-marches this ray in the backward mode
+        }
+    }
 }
 
 // ray of a thread: pinhole pixel (bit-exact float32 recipe of dot_camera) or a buffer entry
@@ -539,11 +595,43 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
     RayOut out;
     out.st[0] = out.st[1] = out.st[2] = out.st[3] = 0;
     if (valid) {
+        if constexpr (MODE == kBwd) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                out.g[ch] = __ldg(io.grad_rgb + 3 * ray + ch);
+                out.rgbf[ch] = __ldg(io.rgb_fwd + 3 * ray + ch);
+            }
+        }
         march_ray<S, K, MODE, EXACT, NT, DEFER, COMP>(tv, rp, io, ray, ow, dw, stack, out);
-        if constexpr (MODE == kFwd) {
+        if constexpr (MODE == kFwd || MODE == kFwdBwd) {
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) io.rgb[3 * ray + ch] = out.rgb[ch];
             if (io.T_final) io.T_final[ray] = out.T;
+        }
+        if constexpr (MODE == kFwdBwd) {
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) io.grad_out[3 * ray + ch] = out.g[ch];
+            if (out.overflow) {  // too many occupied segments to record: march again backward
+                RayOut b;
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) {
+                    b.g[ch] = out.g[ch];
+                    b.rgbf[ch] = out.rgb[ch];
+                }
+                RenderParams rb = rp;
+                rb.signal_mode = DOT_SIGNAL_NONE;
+                RenderIO ib = io;
+                ib.signal = nullptr;
+                march_ray<S, K, kBwd, EXACT, NT, DEFER, COMP>(tv, rb, ib, ray, ow, dw, stack, b);
+            }
+        }
+    }
+    if constexpr (MODE == kFwdBwd) {
+        if (io.loss_sum) {
+            float l = valid ? out.loss : 0.f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+            if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(io.loss_sum, (double)l * io.inv3R);
         }
     }
     if constexpr (MODE == kStats) {

@@ -59,11 +59,11 @@ cudaError_t launch_sk(bool exact, const TreeView &tv, const RaySource &rs, const
             return launch_nt<S, K, MODE, kFwdMinBlocks, kFwdThreads, false, COMP>(exact, tv, rs, rp, io, stream);
     }
     // large backward launches: 128-thread blocks built for 6 per SM (80 registers, 24 warps)
-    if constexpr (MODE == kBwd && DOT_BWD_MINB > 0) {
+    if constexpr ((MODE == kBwd || MODE == kFwdBwd) && DOT_BWD_MINB > 0) {
         if (rs.n_rays >= occupancy_threads())
             return launch_nt<S, K, MODE, DOT_BWD_MINB, 128, false, COMP>(exact, tv, rs, rp, io, stream);
     }
-    constexpr bool defer = MODE == kFwd || MODE == kBwd;
+    constexpr bool defer = MODE == kFwd || MODE == kBwd || MODE == kFwdBwd;
     return launch_nt<S, K, MODE, 1, kMarchThreads, defer, COMP>(exact, tv, rs, rp, io, stream);
 }
 

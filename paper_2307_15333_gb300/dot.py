@@ -40,7 +40,7 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
                 "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize",
-                "dot_rmsprop_step_sparse", "dot_rmsprop_flush")
+                "dot_rmsprop_step_sparse", "dot_rmsprop_flush", "dot_render_forward_backward_mse")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -177,6 +177,8 @@ def lib() -> ctypes.CDLL:
         "dot_tree_canonicalize": [P, P, ctypes.POINTER(dot_leaf_array), ctypes.c_int32, P],
         "dot_rmsprop_step_sparse": [P, P, P, P, P, P, P, ctypes.c_int32, P, ctypes.POINTER(dot_rmsprop_opts), P],
         "dot_rmsprop_flush": [P, P, P, P, ctypes.c_int32, ctypes.POINTER(dot_rmsprop_opts), P],
+        "dot_render_forward_backward_mse": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts),
+                                            P, P, P, P, P, P, P, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -490,6 +492,31 @@ def dot_render_backward(tree: Octree, rays: dot_rays, opts: dot_render_opts,
     _check(lib().dot_render_backward(tree.handle, ctypes.byref(rays), ctypes.byref(opts),
                                      _ptr(grad_rgb), _ptr(rgb), _ptr(grad_sigma), _ptr(grad_sh),
                                      _ptr(signal), _ptr(touched), _stream(stream)))
+
+
+def dot_render_forward_backward_mse(tree: Octree, rays: dot_rays, opts: dot_render_opts,
+                                    target: torch.Tensor, rgb: torch.Tensor,
+                                    grad_rgb: torch.Tensor, grad_sigma: torch.Tensor,
+                                    grad_sh: torch.Tensor, loss_sum: Optional[torch.Tensor] = None,
+                                    signal: Optional[torch.Tensor] = None,
+                                    touched: Optional[torch.Tensor] = None, stream=None):
+    """Forward, MSE gradient and backward of a ray batch in one launch (see dot.h)."""
+    R = n_rays_of(rays)
+    inf = tree.info()
+    for t, n in ((target, "target"), (rgb, "rgb"), (grad_rgb, "grad_rgb")):
+        _need(t, torch.float32, 3 * R, n)
+    _need(grad_sigma, torch.float32, inf.n_leaves, "grad_sigma")
+    _need(grad_sh, torch.float32, inf.n_leaves * 3 * inf.n_coeffs, "grad_sh")
+    if loss_sum is not None:
+        _need(loss_sum, torch.float64, 1, "loss_sum")
+    if signal is not None:
+        _need(signal, torch.float32, inf.n_leaves, "signal")
+    if touched is not None:
+        _need(touched, torch.uint8, inf.n_leaves, "touched")
+    _check(lib().dot_render_forward_backward_mse(
+        tree.handle, ctypes.byref(rays), ctypes.byref(opts), _ptr(target), _ptr(rgb),
+        _ptr(grad_rgb), _ptr(loss_sum), _ptr(grad_sigma), _ptr(grad_sh), _ptr(signal),
+        _ptr(touched), _stream(stream)))
 
 
 def dot_accumulate_signal(tree: Octree, rays: Optional[dot_rays], opts: dot_render_opts,

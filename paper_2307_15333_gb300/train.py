@@ -2,8 +2,9 @@
 
 One optimisation step on a batch of stochastic ray samples (Sec. 4.1):
     forward render with the training signal fused (Sec. 3.1: Q accumulates over the epoch),
-    MSE loss and dL/dC (dot_mse_grad), backward march into FP32 gradients
-    (dot_render_backward, which also flags the leaves it touches), RMSProp update fused with
+    MSE loss and dL/dC, backward into FP32 gradients that also flags the leaves it touches -- by
+    default all three in one launch (dot_render_forward_backward_mse), else as dot_render_forward,
+    dot_mse_grad and dot_render_backward -- then the RMSProp update fused with
     zeroing the gradients (Sec. 3.3, learning rates of Sec. 4.1): by default only over the touched
     leaves, with the pure decay of the others deferred (dot_rmsprop_step_sparse, the same update
     up to FP32 rounding), else over every leaf (dot_rmsprop_step).
@@ -28,9 +29,11 @@ from . import dot
 class Trainer:
     def __init__(self, tree: dot.Octree, opts: dot.dot_render_opts,
                  rms: Optional[dot.dot_rmsprop_opts] = None,
-                 signal_mode: int = dot.DOT_SIGNAL_SUM_ALPHA, stream=None, sparse: bool = True):
+                 signal_mode: int = dot.DOT_SIGNAL_SUM_ALPHA, stream=None, sparse: bool = True,
+                 fused: bool = True):
         self.tree = tree
         self.sparse = sparse
+        self.fused = fused
         self.step_no = 0
         self.opts = dot.render_opts(background=tuple(opts.background), eps_T=opts.eps_T,
                                     color_act=opts.color_act, signal_mode=signal_mode,
@@ -75,14 +78,19 @@ class Trainer:
         self._buffers(R)
         s = self.stream
         sig = self.signal if self.signal_mode != dot.DOT_SIGNAL_NONE else None
-        dot.dot_render_forward(self.tree, rays, self.opts, self.rgb, None, sig, stream=s)
-        dot.dot_mse_grad(self.rgb, target, self.grad_rgb, self.loss_sum, stream=s)
-        plain = dot.render_opts(background=tuple(self.opts.background), eps_T=self.opts.eps_T,
-                                color_act=self.opts.color_act, precision=self.opts.precision,
-                                max_steps=self.opts.max_steps)
-        dot.dot_render_backward(self.tree, rays, plain, self.grad_rgb, self.rgb,
-                                self.grad_sigma, self.grad_sh,
-                                touched=self.touched if self.sparse else None, stream=s)
+        touched = self.touched if self.sparse else None
+        if self.fused:
+            dot.dot_render_forward_backward_mse(self.tree, rays, self.opts, target, self.rgb,
+                                                self.grad_rgb, self.grad_sigma, self.grad_sh,
+                                                self.loss_sum, sig, touched, stream=s)
+        else:
+            dot.dot_render_forward(self.tree, rays, self.opts, self.rgb, None, sig, stream=s)
+            dot.dot_mse_grad(self.rgb, target, self.grad_rgb, self.loss_sum, stream=s)
+            plain = dot.render_opts(background=tuple(self.opts.background), eps_T=self.opts.eps_T,
+                                    color_act=self.opts.color_act, precision=self.opts.precision,
+                                    max_steps=self.opts.max_steps)
+            dot.dot_render_backward(self.tree, rays, plain, self.grad_rgb, self.rgb,
+                                    self.grad_sigma, self.grad_sh, touched=touched, stream=s)
         self.step_no += 1
         if self.sparse:
             dot.dot_rmsprop_step_sparse(self.tree, self.grad_sigma, self.grad_sh, self.ms_sigma,

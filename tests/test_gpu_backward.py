@@ -150,3 +150,69 @@ def test_large_backward_launch_equals_small_launches():
         assert np.abs(a - b).max() <= 1e-5 * scale + 1e-9
     assert tree.status() == 0
     tree.free()
+
+
+def _separate_and_fused(dot, tree, rays, opts_sig, tgt, R, L, K):
+    """The three separate calls (forward with signal, MSE gradient, backward) and the fused pass
+    on the same rays; returns both sets of outputs."""
+    plain = dot.render_opts(background=tuple(opts_sig.background), eps_T=opts_sig.eps_T)
+    z = lambda *s: torch.zeros(*s, device="cuda")
+    a = dict(rgb=z(R, 3), g=z(R, 3), loss=torch.zeros(1, dtype=torch.float64, device="cuda"),
+             gs=z(L), gsh=z(L, 3, K), sig=z(L), touched=torch.zeros(L, dtype=torch.uint8, device="cuda"))
+    dot.dot_render_forward(tree, rays, opts_sig, a["rgb"], None, a["sig"])
+    dot.dot.dot_mse_grad(a["rgb"], tgt, a["g"], a["loss"])
+    dot.dot_render_backward(tree, rays, plain, a["g"], a["rgb"], a["gs"], a["gsh"], touched=a["touched"])
+    b = dict(rgb=z(R, 3), g=z(R, 3), loss=torch.zeros(1, dtype=torch.float64, device="cuda"),
+             gs=z(L), gsh=z(L, 3, K), sig=z(L), touched=torch.zeros(L, dtype=torch.uint8, device="cuda"))
+    dot.dot.dot_render_forward_backward_mse(tree, rays, opts_sig, tgt, b["rgb"], b["g"], b["gs"],
+                                            b["gsh"], b["loss"], b["sig"], b["touched"])
+    torch.cuda.synchronize()
+    return a, b
+
+
+def _assert_same_pass(a, b):
+    assert torch.equal(a["rgb"], b["rgb"])
+    assert torch.equal(a["g"], b["g"])
+    assert torch.equal(a["touched"], b["touched"])
+    assert float(b["loss"]) == pytest.approx(float(a["loss"]), rel=1e-6)
+    for k in ("gs", "gsh", "sig"):
+        x, y = a[k].cpu().numpy().astype(np.float64), b[k].cpu().numpy().astype(np.float64)
+        assert np.abs(x - y).max() <= 1e-5 * max(np.abs(x).max(), 1e-30), k
+
+
+@pytest.mark.parametrize("storage,deg", [(si.STORAGE_F32, 2), (si.STORAGE_F16, 3), (si.STORAGE_BF16, 1)])
+def test_fused_training_pass_equals_separate_calls(storage, deg):
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(45 + deg, max_depth=5, sh_degree=deg, storage=storage, n_prims=4)
+    tree = dot.octree_from_scene(scene)
+    L, K = tree.n_leaves, (deg + 1) ** 2
+    o, d = si.random_rays(5000, 77)
+    R = o.shape[0]
+    rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    tgt = torch.from_numpy(np.random.default_rng(2).random((R, 3)).astype(np.float32)).cuda()
+    opts = dot.render_opts(background=(0.3, 0.3, 0.9), eps_T=1e-4,
+                           signal_mode=dot.dot.DOT_SIGNAL_SUM_ALPHA)
+    a, b = _separate_and_fused(dot, tree, rays, opts, tgt, R, L, K)
+    assert a["touched"].any()
+    _assert_same_pass(a, b)
+    tree.free()
+
+
+def test_fused_training_pass_overflow_rays_march_again():
+    """A dense box filling the root at depth 6 without early termination: rays cross up to ~190
+    occupied cells, beyond the 32-segment record, and take the backward re-march."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.box_scene((-1, -1, -1), (1, 1, 1), max_depth=6, sh_degree=1,
+                         storage=si.STORAGE_F32, density=(0.01, 0.05), sh_std=0.3)
+    tree = dot.octree_from_scene(scene)
+    L, K = tree.n_leaves, 4
+    o, d = si.random_rays(3000, 78)
+    R = o.shape[0]
+    rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    st = dot.dot_render_stats(tree, rays, dot.render_opts(eps_T=0.0))
+    assert st["occupied"] > 40 * st["rays_hit"]
+    tgt = torch.from_numpy(np.random.default_rng(3).random((R, 3)).astype(np.float32)).cuda()
+    opts = dot.render_opts(background=(1, 1, 1), eps_T=0.0, signal_mode=dot.dot.DOT_SIGNAL_MAX_WEIGHT)
+    a, b = _separate_and_fused(dot, tree, rays, opts, tgt, R, L, K)
+    _assert_same_pass(a, b)
+    tree.free()
