@@ -304,7 +304,7 @@ int dot_render_backward(const dot_tree *tree, const dot_rays *rays, const dot_re
  * grad_rgb = 2 (rgb - target) / (3R) (as dot_mse_grad; loss_sum += the MSE), and the backward
  * (as dot_render_backward with that gradient).  Each ray records its occupied segments (weight,
  * transmittance, length, colour) while marching forward and scatters the gradients from that
- * record, so the backward takes no second traversal; a ray with more than 32 occupied segments
+ * record, so the backward takes no second traversal; a ray with more than 48 occupied segments
  * marches again in the backward mode.  Results equal the three separate calls up to the order
  * of the FP32 atomic sums.
  * target, rgb, grad_rgb: device [R][3] float (rgb and grad_rgb written, all distinct);

@@ -75,7 +75,7 @@ struct RenderIO {
 // march again in the backward mode).
 enum MarchMode : int { kFwd = 0, kBwd = 1, kSignal = 2, kStats = 3, kFwdBwd = 4 };
 #ifndef DOT_RECORD_SEGMENTS
-#define DOT_RECORD_SEGMENTS 32
+#define DOT_RECORD_SEGMENTS 48
 #endif
 constexpr int kRecordSegments = DOT_RECORD_SEGMENTS;
 
