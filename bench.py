@@ -306,7 +306,9 @@ def measure_compressed(scene, cams, steps: int):
     stream = torch.cuda.current_stream()
     tree = dot.octree_from_scene(scene)
     W, H = cams[0].width, cams[0].height
-    rays = dot.rays_cameras(dot.cameras_tensor(cams), W, H)
+    cam_t = dot.cameras_tensor(cams)
+    order_t = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
+    rays = dot.rays_cameras(cam_t, W, H, order_t)
     R = len(cams) * W * H
     opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
     ref = torch.empty(R, 3, device="cuda")
@@ -349,7 +351,8 @@ def measure_tanks_temples(steps: int):
     tree = dot.octree_from_scene(scene)
     W, H = cams[0].width, cams[0].height
     cam_t = dot.cameras_tensor(cams)
-    rays = dot.rays_cameras(cam_t, W, H)
+    order_t = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
+    rays = dot.rays_cameras(cam_t, W, H, order_t)
     R = len(cams) * W * H
     opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
     rgb = torch.empty(R, 3, device="cuda")
@@ -451,7 +454,9 @@ def run_dot(args):
     tree = dot.octree_from_scene(scene)
     L = tree.n_leaves
     cam_t = dot.cameras_tensor(cams)
-    rays = dot.rays_cameras(cam_t, W, H)
+    # views rendered in a nearest-neighbour chain so that consecutive views reuse L2
+    order_t = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
+    rays = dot.rays_cameras(cam_t, W, H, order_t)
     R = len(cams) * W * H
     opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
     rgb = torch.empty(R, 3, dtype=torch.float32, device="cuda")
@@ -577,7 +582,7 @@ def run_dot(args):
         render_views(tree, cams_host, W, H, opts, out_host)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": R * e2e_steps * ws / e2e_s / 1e6, "unit": "Mrays/s",
-           "h2d_bytes_per_step": int(cams_host.numel() * 4),
+           "h2d_bytes_per_step": int(cams_host.numel() * 4 + cams_host.shape[0] * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 4)}
 
     # ---- refine pass (signal, selection, prune / sample), once, on the resident tree ----

@@ -82,6 +82,7 @@ extern "C" {
 #define DOT_PRECISION_EXACT 2 /* float-float plane times and full-precision exponentials */
 
 #define DOT_STATUS_STEP_LIMIT 1u /* a ray hit the step cap; its output is truncated */
+#define DOT_STATUS_BAD_INPUT 2u  /* a device-side input was out of range and was skipped */
 
 typedef struct dot_tree dot_tree;
 
@@ -168,6 +169,11 @@ typedef struct {
     int64_t n_rays;            /* BUFFER */
     const float *origins;      /* BUFFER: device [n_rays][3] */
     const float *dirs;         /* BUFFER: device [n_rays][3], unit length */
+    const int32_t *view_order; /* CAMERAS: device [n_cameras] or NULL -- the order in which the
+                                  views are rendered (a permutation; ray ids are unchanged).  A
+                                  locality-friendly order (dot_camera_order) lets consecutive views
+                                  reuse the leaves left in L2.  Entries out of range are skipped
+                                  and set DOT_STATUS_BAD_INPUT */
 } dot_rays;
 
 #define DOT_MAX_SERVE_TREES 8
@@ -259,6 +265,13 @@ int dot_tree_import(const dot_host_tree *host, const dot_allocator *alloc, void 
 /* Synchronises the stream, returns the tree's device status bits (DOT_STATUS_*) and clears
  * them. */
 int dot_tree_status(dot_tree *tree, void *stream, uint32_t *status);
+
+/*
+ * dot_camera_order -- a rendering order for n cameras (HOST array) in which consecutive views are
+ * close: a greedy nearest-neighbour chain over the camera positions starting at camera 0.  Written
+ * to order[n] (host); pass it (copied to the device) as dot_rays.view_order.
+ */
+int dot_camera_order(const dot_camera *cameras, int32_t n, int32_t *order);
 
 /*
  * dot_render_forward -- Eq. 1-2 per ray: the ray's segments through the leaves in order,

@@ -165,6 +165,7 @@ int make_rays(const dot_rays *rays, dot::RaySource &rs, int64_t &n_rays) {
         if (rays->width <= 0 || rays->height <= 0 || rays->width > 65536 || rays->height > 65536)
             return fail(DOT_ERR_INVALID_ARG, "camera width / height out of range");
         rs.cams = rays->cameras;
+        rs.order = rays->view_order;
         rs.n_cams = rays->n_cameras;
         rs.width = rays->width;
         rs.height = rays->height;
@@ -816,5 +817,34 @@ extern "C" int dot_render_forward_backward_mse(const dot_tree *t, const dot_rays
     API_CK(dot::launch_march_fwdbwd(t->a.storage, t->a.sh_degree, exact, view_of(t), rs, rp, io,
                                     S(stream)),
            "dot_render_forward_backward_mse");
+    return DOT_OK;
+}
+
+extern "C" int dot_camera_order(const dot_camera *cams, int32_t n, int32_t *order) {
+    if (n < 0) return fail(DOT_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return DOT_OK;
+    if (!cams || !order) return fail(DOT_ERR_INVALID_ARG, "cameras and order are required");
+    std::vector<char> used((size_t)n, 0);
+    int32_t cur = 0;
+    used[0] = 1;
+    order[0] = 0;
+    for (int32_t k = 1; k < n; k++) {
+        const float *a = cams[cur].c2w;
+        double best = -1.0;
+        int32_t bi = -1;
+        for (int32_t j = 0; j < n; j++) {
+            if (used[(size_t)j]) continue;
+            const float *b = cams[j].c2w;
+            const double dx = (double)b[3] - a[3], dy = (double)b[7] - a[7], dz = (double)b[11] - a[11];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (bi < 0 || d2 < best) {
+                best = d2;
+                bi = j;
+            }
+        }
+        used[(size_t)bi] = 1;
+        order[k] = bi;
+        cur = bi;
+    }
     return DOT_OK;
 }

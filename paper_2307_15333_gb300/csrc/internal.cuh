@@ -39,6 +39,7 @@ struct RaySource {
     int32_t n_cams, width, height;
     int32_t tiles_x;           // ceil(width / 16)
     const dot_camera *cams;
+    const int32_t *order;      // CAMERAS: view rendered by block row y, or null (identity)
     const float *origins, *dirs;
     int64_t n_rays;
 };

@@ -579,8 +579,16 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
         const int px = tx * TL::kW + (warp % (TL::kW / 8)) * 8 + (lane & 7);
         const int py = ty * TL::kH + (warp / (TL::kW / 8)) * 4 + (lane >> 3);
         valid = px < rs.width && py < rs.height;
-        ray = ((int64_t)blockIdx.y * rs.height + py) * rs.width + px;
-        if (valid) camera_ray(rs.cams + blockIdx.y, px, py, ow, dw);
+        int v = blockIdx.y;
+        if (rs.order) {
+            v = __ldg(rs.order + blockIdx.y);
+            if (v < 0 || v >= rs.n_cams) {
+                if (threadIdx.x == 0) atomicOr(io.status, DOT_STATUS_BAD_INPUT);
+                return;
+            }
+        }
+        ray = ((int64_t)v * rs.height + py) * rs.width + px;
+        if (valid) camera_ray(rs.cams + v, px, py, ow, dw);
     } else {
         ray = (int64_t)blockIdx.x * NT + threadIdx.x;
         valid = ray < rs.n_rays;

@@ -33,6 +33,7 @@ DOT_MERGE_MEAN, DOT_MERGE_SUM, DOT_MERGE_MAX = 0, 1, 2
 DOT_RAYS_BUFFER, DOT_RAYS_CAMERAS = 0, 1
 DOT_PRECISION_AUTO, DOT_PRECISION_FAST, DOT_PRECISION_EXACT = 0, 1, 2
 DOT_STATUS_STEP_LIMIT = 1
+DOT_STATUS_BAD_INPUT = 2
 
 ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_free",
                 "dot_tree_get_info", "dot_tree_export", "dot_tree_import", "dot_tree_status",
@@ -40,7 +41,8 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_select_masks", "dot_refine_plan", "dot_refine_prune", "dot_render_stats",
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
                 "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize",
-                "dot_rmsprop_step_sparse", "dot_rmsprop_flush", "dot_render_forward_backward_mse")
+                "dot_rmsprop_step_sparse", "dot_rmsprop_flush", "dot_render_forward_backward_mse",
+                "dot_camera_order")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -107,7 +109,7 @@ class dot_camera(ctypes.Structure):
 class dot_rays(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n_cameras", ctypes.c_int32), ("cameras", P),
                 ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_rays", ctypes.c_int64),
-                ("origins", P), ("dirs", P)]
+                ("origins", P), ("dirs", P), ("view_order", P)]
 
 
 class dot_render_opts(ctypes.Structure):
@@ -179,6 +181,7 @@ def lib() -> ctypes.CDLL:
         "dot_rmsprop_flush": [P, P, P, P, ctypes.c_int32, ctypes.POINTER(dot_rmsprop_opts), P],
         "dot_render_forward_backward_mse": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts),
                                             P, P, P, P, P, P, P, P, P],
+        "dot_camera_order": [P, ctypes.c_int32, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -398,7 +401,10 @@ def cameras_tensor(cams: Sequence, device="cuda") -> torch.Tensor:
     return torch.from_numpy(arr).to(device)
 
 
-def rays_cameras(cams: torch.Tensor, width: int, height: int) -> dot_rays:
+def rays_cameras(cams: torch.Tensor, width: int, height: int,
+                 view_order: Optional[torch.Tensor] = None) -> dot_rays:
+    """Camera rays of every [n, 18] dot_camera record (device); view_order: optional device
+    int32 [n] permutation in which the views are rendered (ray ids unchanged)."""
     _need(cams, torch.float32, name="cameras")
     if cams.dim() != 2 or cams.shape[1] != 18:
         raise ValueError("cameras must be [n, 18] float32 records")
@@ -408,8 +414,19 @@ def rays_cameras(cams: torch.Tensor, width: int, height: int) -> dot_rays:
     r.cameras = _ptr(cams)
     r.width, r.height = int(width), int(height)
     r.n_rays = 0
-    r._keep = cams
+    if view_order is not None:
+        _need(view_order, torch.int32, cams.shape[0], "view_order")
+        r.view_order = _ptr(view_order)
+    r._keep = (cams, view_order)
     return r
+
+
+def dot_camera_order(cams_host: np.ndarray) -> np.ndarray:
+    """Nearest-neighbour chain order of the cameras ([n, 18] float32 host records)."""
+    c = np.ascontiguousarray(cams_host, dtype=np.float32).reshape(-1, 18)
+    order = np.zeros(c.shape[0], np.int32)
+    _check(lib().dot_camera_order(c.ctypes.data_as(P), c.shape[0], order.ctypes.data_as(P)))
+    return order
 
 
 def n_rays_of(r: dot_rays) -> int:

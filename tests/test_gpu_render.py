@@ -163,3 +163,37 @@ def test_step_cap_sets_status_without_hanging():
     _gpu_render(tree, o, d)
     assert tree.status() == 0
     tree.free()
+
+
+def test_view_order_renders_the_same_rays():
+    """A view order changes only the schedule: the images are identical bit for bit; an order
+    entry out of range skips its views and sets DOT_STATUS_BAD_INPUT."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(12, max_depth=5, sh_degree=2, storage=si.STORAGE_F16, n_prims=4)
+    tree = dot.octree_from_scene(scene)
+    cams = [si.pinhole((3 * np.cos(a), 1.0, 3 * np.sin(a)), 320, 240, 300.0)
+            for a in np.linspace(0, 6, 7)]
+    recs = np.stack([c.packed() for c in cams])
+    cam_t = dot.cameras_tensor(cams)
+    R = 7 * 320 * 240
+    opts = dot.render_opts(background=(1, 1, 1))
+    a = torch.empty(R, 3, device="cuda")
+    b = torch.full((R, 3), -1.0, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 320, 240), opts, a)
+    order = torch.from_numpy(dot.dot.dot_camera_order(recs)).cuda()
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 320, 240, order), opts, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert tree.status() == 0
+    bad = order.clone()
+    bad[3] = 7
+    c = torch.full((R, 3), -1.0, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 320, 240, bad), opts, c)
+    torch.cuda.synchronize()
+    assert tree.status() == dot.dot.DOT_STATUS_BAD_INPUT
+    skipped = int(order[3])
+    img = c.view(7, 240 * 320, 3)
+    assert (img[skipped] == -1.0).all()
+    others = [v for v in range(7) if v != skipped]
+    assert torch.equal(img[others], a.view(7, -1, 3)[others])
+    tree.free()
