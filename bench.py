@@ -124,11 +124,14 @@ MARCH_SOURCES = ("internal.cuh", "march.cuh", "march_launch.cuh", "render_fwd.cu
 
 
 def csrc_hash() -> str:
+    """Hash of the code (comments and whitespace removed) of the forward march's sources."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2307_15333_gb300", "csrc")
     for f in MARCH_SOURCES:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(d, f)) as fh:
+            code = re.sub(r"/\*.*?\*/", " ", fh.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(f.encode() + " ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -75,6 +75,9 @@ struct RenderIO {
 // backward needs no second traversal (rays with more occupied segments than the record holds
 // march again in the backward mode).
 enum MarchMode : int { kFwd = 0, kBwd = 1, kSignal = 2, kStats = 3, kFwdBwd = 4 };
+// occupied segments a ray of the fused pass records (32 bytes each, local memory); the rays that
+// overflow it are the longest ones, so it is sized above the 99.9th percentile of training rays
+// (build-time tunable: -DDOT_RECORD_SEGMENTS=n)
 #ifndef DOT_RECORD_SEGMENTS
 #define DOT_RECORD_SEGMENTS 48
 #endif
@@ -83,10 +86,6 @@ constexpr int kRecordSegments = DOT_RECORD_SEGMENTS;
 // ---------------------------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------------------------
-
-cudaError_t launch_march(int mode, int storage, int sh_degree, bool exact, const TreeView &tv,
-                         const RaySource &rs, const RenderParams &rp, const RenderIO &io,
-                         cudaStream_t stream);
 
 cudaError_t launch_sigma_signal(int storage, const void *sigma, int64_t n, float *signal,
                                 cudaStream_t stream);

@@ -3,6 +3,8 @@
 
 #include "march.cuh"
 
+// Build-time launch shapes (measured on a GB300 on the 64 M-ray workloads; -D to override):
+// threads per block of large forward launches, and blocks per SM of large backward launches.
 #ifndef DOT_FWD_NT
 #define DOT_FWD_NT 128
 #endif
