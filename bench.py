@@ -149,44 +149,63 @@ def profiled_traffic(kernel_tag: str):
     return float(m.group(1))
 
 
-def oracle_baseline(scene, cams, budget_s: float, threads: int):
-    """The FP64 oracle as it stands, timed on the host cores over a strided pixel sample."""
-    import oracle
-    import seeded_inputs as si
-    t = oracle.scene_tree(scene)
-    sig, sh = si.leaf_params(t["leaf_key"], t["leaf_inside"], scene)
-    s64, h64 = si.storage_to_f64(sig, scene.storage), si.storage_to_f64(sh, scene.storage)
-    lo, size = oracle.root_of(scene)
-    W, H = cams[0].width, cams[0].height
-    # calibrate on growing samples (until one takes a second), then size the measured sample
-    stride = 4096
-    while True:
-        pix = np.arange(0, W * H, stride)
-        o, d = si.camera_rays(cams[0], pix)
+class OracleSample:
+    """The FP64 oracle as it stands, on the host cores, over a strided pixel sample of the views
+    sized to a time budget (the oracle's tree and parameters are built once)."""
+
+    def __init__(self, scene, cams):
+        import oracle
+        import seeded_inputs as si
+        self.oracle, self.si = oracle, si
+        self.scene, self.cams = scene, cams
+        self.t = oracle.scene_tree(scene)
+        sig, sh = si.leaf_params(self.t["leaf_key"], self.t["leaf_inside"], scene)
+        self.s64 = si.storage_to_f64(sig, scene.storage)
+        self.h64 = si.storage_to_f64(sh, scene.storage)
+        self.lo, self.size = oracle.root_of(scene)
+
+    def _render(self, o, d, threads):
+        self.oracle.render(self.t, self.lo, self.size, self.s64, self.h64, self.scene.sh_degree,
+                           o, d, threads=threads)
+
+    def rays(self, budget_s: float, threads: int):
+        """A strided sample of every view whose render takes about budget_s."""
+        W, H = self.cams[0].width, self.cams[0].height
+        stride = 4096
+        while True:          # calibrate on growing samples until one takes a second
+            pix = np.arange(0, W * H, stride)
+            o, d = self.si.camera_rays(self.cams[0], pix)
+            t0 = time.perf_counter()
+            self._render(o, d, threads)
+            dt = max(time.perf_counter() - t0, 1e-6)
+            if dt > 1.0 or stride == 1:
+                break
+            stride = max(1, stride // 4)
+        rate = len(pix) / dt
+        want = max(1000, int(rate * budget_s))
+        stride = max(1, (W * H * len(self.cams)) // want)
+        os_, ds_ = [], []
+        for v, cam in enumerate(self.cams):
+            o, d = self.si.camera_rays(cam, np.arange(v % stride, W * H, stride))
+            os_.append(o)
+            ds_.append(d)
+        which = "every pixel" if stride == 1 else f"every {stride}-th pixel"
+        desc = f"{which} of the {len(self.cams)} {W}x{H} views"
+        return np.concatenate(os_), np.concatenate(ds_), desc
+
+    def time(self, o, d, threads):
         t0 = time.perf_counter()
-        oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
-        dt = max(time.perf_counter() - t0, 1e-6)
-        if dt > 1.0 or stride == 1:
-            break
-        stride = max(1, stride // 4)
-    rate = len(pix) / dt
-    n_views = len(cams)
-    want = max(1000, int(rate * budget_s))
-    stride = max(1, (W * H * n_views) // want)
-    os_, ds_ = [], []
-    for v in range(n_views):
-        p = np.arange(v % stride, W * H, stride)
-        o, d = si.camera_rays(cams[v], p)
-        os_.append(o)
-        ds_.append(d)
-    o, d = np.concatenate(os_), np.concatenate(ds_)
-    t0 = time.perf_counter()
-    oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, threads=threads)
-    dt = time.perf_counter() - t0
-    which = "every pixel" if stride == 1 else f"every {stride}-th pixel"
+        self._render(o, d, threads)
+        return time.perf_counter() - t0
+
+
+def oracle_baseline(scene, cams, budget_s: float, threads: int, sampler=None):
+    """The oracle timed once on a sample of about budget_s seconds."""
+    sm = sampler or OracleSample(scene, cams)
+    o, d, desc = sm.rays(budget_s, threads)
+    dt = sm.time(o, d, threads)
     return {"value": o.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": f"{which} of the {n_views} 800x800 views "
-                      f"({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
+            "sample": f"{desc} ({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
 
 
 def measure_serving(args):
@@ -283,7 +302,7 @@ def measure_training(scene, cams, steps: int):
     q = float(torch.quantile(tr.signal[tr.signal > 0].float()[:1 << 24], 0.2))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = tr.refine(q, 0.05, depth_cap=11, recursive=True)
+    res = tr.refine(q, 0.05, depth_cap=11, recursive=True, canonical=True)
     torch.cuda.synchronize()
     refine_ms = (time.perf_counter() - t0) * 1e3
     out = {"value": BATCH * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "iters_per_s": n / (ms / 1e3),
@@ -292,7 +311,9 @@ def measure_training(scene, cams, steps: int):
                    "deferred decay)+zero grad",
            "refine": {"ms": refine_ms, "tau": q, "gamma": 0.05, "recursive": True,
                       "pruned_groups_per_pass": [p["n_pruned_groups"] for p in res["passes"]],
-                      "leaves_after": res["n_leaves"]}}
+                      "leaves_after": res["n_leaves"]},
+           # the training schedule of the workload: a refine every 1000 iterations
+           "iters_per_s_with_refine_every_1000": 1000.0 / ((1000 * ms / n + refine_ms) / 1e3)}
     tree.free()
     return out
 
@@ -406,16 +427,21 @@ def run_reference(args):
     import seeded_inputs as si
     scene, cams = si.config_nerf_synthetic(args.views)
     threads = os.cpu_count() or 1
-    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    # every step renders the same bounded sample; the whole run stays within about a minute or two
+    per_step = min(2.0, max(0.25, args.cpu_seconds / max(1, args.steps)))
+    sm = OracleSample(scene, cams)
+    o, d, desc = sm.rays(per_step, threads)
     vals = []
     for i in range(args.warmup + args.steps):
-        b = oracle_baseline(scene, cams, per_step, threads)
+        dt = sm.time(o, d, threads)
         if i >= args.warmup:
-            vals.append(b)
+            vals.append({"value": o.shape[0] / dt / 1e6, "ms": dt * 1e3,
+                         "sample": f"{desc} ({o.shape[0]} rays, FP64 forward render, {dt:.2f} s)"})
     v = statistics.median([b["value"] for b in vals])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.median([b["ms"] for b in vals]),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": vals[-1]["sample"]},
             "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
@@ -605,6 +631,22 @@ def run_dot(args):
     refine_ms = (time.perf_counter() - t0) * 1e3
     refine = {"ms": refine_ms, "leaves_before": L, "leaves_after": counts["n_leaves"],
               "signal": f"MAX_WEIGHT over {nb} x 2^16 rays", "select": "bottom 20% / top 5%"}
+    # the refined tree keeps its cells in appended order; renumbering restores Morton order
+    rgb2 = torch.empty(R, 3, dtype=torch.float32, device="cuda")
+    dot.dot_render_forward(tree, rays, opts, rgb2)
+    torch.cuda.synchronize()
+    ms_app = timed(lambda i: dot.dot_render_forward(tree, rays, opts, rgb2), 5, stream) / 5
+    perm = torch.empty(counts["n_leaves"], dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    dot.dot.dot_tree_canonicalize(tree, perm)
+    torch.cuda.synchronize()
+    canon_ms = (time.perf_counter() - t0) * 1e3
+    dot.dot_render_forward(tree, rays, opts, rgb2)
+    torch.cuda.synchronize()
+    ms_can = timed(lambda i: dot.dot_render_forward(tree, rays, opts, rgb2), 5, stream) / 5
+    refine["forward_after_refine_ms"] = {"appended_order": ms_app, "canonical_order": ms_can,
+                                         "canonicalize_ms": canon_ms}
+    del rgb2, perm
 
     serve_res = measure_serving(args) if rank == 0 else None
     train_res = measure_training(scene, cams, args.steps) if rank == 0 and not args.quick else None
@@ -625,8 +667,9 @@ def run_dot(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(scene, cams, args.cpu_seconds, os.cpu_count() or 1)
-        cpu["single_thread"] = oracle_baseline(scene, cams, 2.0, 1)
+        sampler = OracleSample(scene, cams)
+        cpu = oracle_baseline(scene, cams, args.cpu_seconds, os.cpu_count() or 1, sampler)
+        cpu["single_thread"] = oracle_baseline(scene, cams, 2.0, 1, sampler)
 
     line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

@@ -184,7 +184,7 @@ typedef struct {
     dot_camera camera;
     int32_t tree;
     int32_t pad_;
-    int64_t tile_begin; /* sum of ceil(W/16) ceil(H/16) over the slots before this one */
+    int64_t tile_begin; /* sum of ceil(W/16) ceil(H/8) over the slots before this one */
     float *out;
 } dot_slot;
 
@@ -286,7 +286,7 @@ int dot_render_forward(const dot_tree *tree, const dot_rays *rays, const dot_ren
 /*
  * dot_render_slots -- renders every request of a device slot table in one persistent launch
  * (Eq. 1-2 per pixel, as dot_render_forward): the requests may differ in resolution and in the
- * tree they look at.  Blocks take 16x16 tiles from a work counter until the table's tiles run out;
+ * tree they look at.  Blocks take 16x8 tiles from a work counter until the table's tiles run out;
  * each pixel's value does not depend on the other requests in the table.
  * trees[n_trees] (1..DOT_MAX_SERVE_TREES, host array of handles): resident trees sharing one
  * storage type and SH degree.  table: device dot_slot_table_header + max_slots dot_slot (read by

@@ -1,11 +1,11 @@
 // render_slots.cu -- one persistent launch rendering many camera requests (mixed resolutions,
 // several resident trees) from a device slot table.
 //
-// Every request is cut into 16x16 pixel tiles; tile t of the launch belongs to the slot whose
-// tile_begin is the largest one <= t.  A grid of (SMs x resident blocks) blocks pulls tiles from
-// one device counter until it passes total_tiles, then exits: there is no waiting on flags.  Each
-// pixel runs the same march as dot_render_forward, so a request's image does not depend on what
-// else shares the launch.
+// Every request is cut into 16x8 pixel tiles (four warps of 8x4 pixels, the tiles of the large
+// forward launches); tile t of the launch belongs to the slot whose tile_begin is the largest one
+// <= t.  A grid of (SMs x resident blocks) blocks pulls tiles from one device counter until it
+// passes total_tiles, then exits: there is no waiting on flags.  Each pixel runs the same march
+// as dot_render_forward, so a request's image does not depend on what else shares the launch.
 #include "march.cuh"
 
 namespace dot {
@@ -23,11 +23,13 @@ struct SlotHeader {
     int64_t total_tiles;
 };
 
+constexpr int kSlotThreads = 128;
+
 template <typename S, int K, bool EXACT, bool COMP>
-__global__ void __launch_bounds__(kMarchThreads, 4)
+__global__ void __launch_bounds__(kSlotThreads, 8)
 slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots, RenderParams rp,
              unsigned long long *__restrict__ counter, uint32_t *status) {
-    __shared__ int32_t s_stack[kMaxLevels * kMarchThreads];
+    __shared__ int32_t s_stack[kMaxLevels * kSlotThreads];
     __shared__ long long s_tile;
     int32_t *stack = s_stack + threadIdx.x;
     const SlotHeader *hdr = reinterpret_cast<const SlotHeader *>(table);
@@ -53,19 +55,19 @@ slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots,
         }
         const dot_slot *sl = slots + lo;
         const int W = sl->camera.width, H = sl->camera.height;
-        const int tx_n = (W + 15) / 16, ty_n = (H + 15) / 16;
+        const int tx_n = (W + 15) / 16, ty_n = (H + 7) / 8;
         const long long local = tile - sl->tile_begin;
         const int tr = sl->tree;
         if (local < 0 || local >= (long long)tx_n * ty_n || tr < 0 || tr >= trees.n) continue;
         const int tx = (int)(local % tx_n), ty = (int)(local / tx_n);
         const int px = tx * 16 + (warp & 1) * 8 + (lane & 7);
-        const int py = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+        const int py = ty * 8 + (warp >> 1) * 4 + (lane >> 3);
         if (px < W && py < H) {
             float ow[3], dw[3];
             camera_ray(&sl->camera, px, py, ow, dw);
             RayOut out;
-            march_ray<S, K, kFwd, EXACT, kMarchThreads, false, COMP>(trees.t[tr], rp, io, 0, ow,
-                                                                      dw, stack, out);
+            march_ray<S, K, kFwd, EXACT, kSlotThreads, false, COMP>(trees.t[tr], rp, io, 0, ow,
+                                                                     dw, stack, out);
             float *dst = sl->out + ((int64_t)py * W + px) * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) dst[ch] = out.rgb[ch];
@@ -82,10 +84,10 @@ cudaError_t launch_slots_sk(const SlotTrees &trees, const void *table, int32_t m
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slots_kernel<S, K, EXACT, COMP>,
-                                                      kMarchThreads, 0);
+                                                      kSlotThreads, 0);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
-    slots_kernel<S, K, EXACT, COMP><<<grid, kMarchThreads, 0, s>>>(
+    slots_kernel<S, K, EXACT, COMP><<<grid, kSlotThreads, 0, s>>>(
         trees, reinterpret_cast<const char *>(table), max_slots, rp, counter, status);
     return cudaGetLastError();
 }

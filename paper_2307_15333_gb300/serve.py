@@ -2,7 +2,7 @@
 
 Requests (a tree, a camera pose, a resolution) arrive over time.  The batched server admits
 waiting requests into free slots whenever a slot table is free and the output pool has room,
-packs them into a slot table (16x16 tiles of every request numbered consecutively), and replays a
+packs them into a slot table (16x8 tiles of every request numbered consecutively), and replays a
 CUDA graph captured once per table: host-to-device copy of the table, then dot_render_slots (one
 persistent launch that drains the tiles of all admitted requests).  Two tables are in flight at
 a time on two streams, so requests that arrive while a batch is on the GPU start in the next one
@@ -24,7 +24,7 @@ import numpy as np
 
 SLOT_BYTES = 96
 HEADER_BYTES = 16
-TILE = 16
+TILE_W, TILE_H = 16, 8       # the work tile of a slot launch
 
 
 @dataclasses.dataclass
@@ -44,7 +44,7 @@ class Request:
 
     @property
     def tiles(self) -> int:
-        return ((self.width + TILE - 1) // TILE) * ((self.height + TILE - 1) // TILE)
+        return ((self.width + TILE_W - 1) // TILE_W) * ((self.height + TILE_H - 1) // TILE_H)
 
 
 class OutputPool:

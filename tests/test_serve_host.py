@@ -37,7 +37,7 @@ def test_pack_table_layout():
         assert rec[80:88].view(np.int64)[0] == begin
         assert rec[88:96].view(np.uint64)[0] == (1 << 20) + 4 * r.offset
         begin += tiles[i]
-    assert reqs[0].tiles == 7 * 4
+    assert reqs[0].tiles == 7 * 7          # ceil(100 / 16) x ceil(50 / 8)
 
 
 def test_poisson_trace_is_seeded_and_has_the_rate():
