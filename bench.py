@@ -110,6 +110,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(rays_per_rank_step: int, steps: int, ws: int, total_ms: float) -> float:
+    """Whole-job Mrays/s: every rank renders its own copy of the workload (weak scaling), so the
+    job processes ws times the rays of one rank in the slowest rank's time."""
+    return rays_per_rank_step * steps * ws / (total_ms / 1e3) / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -472,11 +489,7 @@ def run_dot(args):
             tdist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return globals()["max_over_ranks"](x, ws)
 
     scene, cams = si.config_nerf_synthetic(args.views)
     W, H = cams[0].width, cams[0].height
@@ -521,7 +534,7 @@ def run_dot(args):
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     total_ms = max_over_ranks(total_ms)
-    value = R * args.steps * ws / (total_ms / 1e3) / 1e6
+    value = weak_scaling_value(R, args.steps, ws, total_ms)
     mean_launch_s = statistics.mean(launch_ms) / 1e3
     assert tree.status() == 0
     # distinct occupied leaves one launch touches (a max-weight signal pass, not timed)
