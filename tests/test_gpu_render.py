@@ -107,14 +107,17 @@ def test_edge_cases():
 
 def test_full_size_nerf_synthetic_sampled_pixels():
     """Config at full size (2.9M leaves, 800x800 views) in the bench's launch configuration
-    (camera mode, all views in one launch); sampled pixels against the oracle."""
+    (camera mode, all views in one launch, nearest-neighbour view order); sampled pixels against
+    the oracle."""
     import paper_2307_15333_gb300 as dot
     scene, cams = si.config_nerf_synthetic(n_views=100)
     tree = dot.octree_from_scene(scene)
     cam_t = dot.cameras_tensor(cams)
+    order = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
     R = 100 * 800 * 800
     rgb = torch.empty(R, 3, device="cuda")
-    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 800, 800), dot.render_opts(), rgb)
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 800, 800, order), opts, rgb)
     torch.cuda.synchronize()
     assert tree.status() == 0
     t, _, _, s64, h64 = oracle_side(scene)
@@ -135,9 +138,10 @@ def test_full_size_tanks_temples_sampled_pixels():
     scene, cams = si.config_tanks_temples(n_views=6)
     tree = dot.octree_from_scene(scene)
     cam_t = dot.cameras_tensor(cams)
+    order = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
     R = 6 * 1920 * 1080
     rgb = torch.empty(R, 3, device="cuda")
-    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 1920, 1080), dot.render_opts(), rgb)
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 1920, 1080, order), dot.render_opts(), rgb)
     torch.cuda.synchronize()
     t, _, _, s64, h64 = oracle_side(scene)
     lo, size = oracle.root_of(scene)
