@@ -284,6 +284,35 @@ int dot_render_forward(const dot_tree *tree, const dot_rays *rays, const dot_ren
                        float *rgb, float *T_final, float *signal, void *stream);
 
 /*
+ * dot_render_views_host -- dot_render_forward over n_cameras whole camera views whose cameras and
+ * images live in HOST memory (Eq. 1-2 per pixel; every value equals dot_render_forward's for the
+ * same camera).  The views are rendered in chunks of about 2^23 rays (the views left after the
+ * full chunks in halving chunks down to one view), in view_order when given so that consecutive
+ * views reuse the leaves left in L2, alternately on `stream` and on a second render stream, into
+ * a ring of three chunk buffers in the workspace; each finished chunk is copied to the host on a
+ * copy stream while the next chunks render, so the device-to-host copy overlaps the march.  The
+ * work is ordered after what `stream` already holds; the call returns after every image is in
+ * rgb (and T_final).
+ * cameras: host [n_cameras] dot_camera (copied to the workspace by this call).  width, height: the
+ * resolution shared by every camera.  view_order: host [n_cameras] or NULL -- the render order, a
+ * permutation of 0..n_cameras-1 (anything else fails with DOT_ERR_INVALID_ARG before any work).
+ * rgb: host [n_cameras][height][width][3] float (written); T_final: host [n_cameras][height][width]
+ * float or NULL.  Page-locked host buffers (cudaHostAlloc, cudaHostRegister) let the copies run
+ * asynchronously at the link's speed; pageable ones work, through the driver's staging copies.
+ * workspace: device buffer owned by the caller, 256-byte aligned, of at least
+ * dot_render_views_host_workspace(n_cameras, width, height, T_final != NULL) bytes; no other work
+ * may use it until this call returns.  opts->signal_mode must be NONE.
+ */
+int dot_render_views_host(const dot_tree *tree, const dot_camera *cameras, int32_t n_cameras,
+                          int32_t width, int32_t height, const int32_t *view_order,
+                          const dot_render_opts *opts, float *rgb, float *T_final,
+                          void *workspace, int64_t workspace_bytes, void *stream);
+
+/* Workspace bytes dot_render_views_host needs (host arithmetic only; -1 for invalid sizes). */
+int64_t dot_render_views_host_workspace(int32_t n_cameras, int32_t width, int32_t height,
+                                        int32_t with_T);
+
+/*
  * dot_render_slots -- renders every request of a device slot table in one persistent launch
  * (Eq. 1-2 per pixel, as dot_render_forward): the requests may differ in resolution and in the
  * tree they look at.  Blocks take 16x8 tiles from a work counter until the table's tiles run out;

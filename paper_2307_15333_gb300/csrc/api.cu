@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" entry points of libdot (include/dot.h): argument checks on the host,
 // tree lifecycle, import / export, and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -846,5 +847,213 @@ extern "C" int dot_camera_order(const dot_camera *cams, int32_t n, int32_t *orde
         order[k] = bi;
         cur = bi;
     }
+    return DOT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// whole views to host memory: chunked march on the caller's stream (and a second render stream),
+// device-to-host copies of the finished chunks on a copy stream
+// ---------------------------------------------------------------------------------------------
+// log2 of the rays per chunk, about
+#ifndef DOT_VIEWS_CHUNK_LOG2
+#define DOT_VIEWS_CHUNK_LOG2 23
+#endif
+// render streams the chunks alternate over (1 or 2): with 2, a chunk's launch starts while the
+// previous chunk's last blocks still run
+#ifndef DOT_VIEWS_STREAMS
+#define DOT_VIEWS_STREAMS 2
+#endif
+// 1: the views left after the full chunks go in halving chunks down to one view, so the copy
+// that cannot overlap any march (the last chunk's) is one view.  100 views of 800x800 on a
+// 2.9 M-leaf tree, 9.81 ms in one launch: 10.90 ms to host memory with one stream and no taper,
+// 10.31 with two streams, 10.14 with two streams and the taper (chunks of 2^22 rays: 10.20).
+#ifndef DOT_VIEWS_TAPER
+#define DOT_VIEWS_TAPER 1
+#endif
+
+namespace {
+
+constexpr int kViewSlots = 3;  // chunk buffers in the ring
+constexpr int64_t kChunkRays = (int64_t)1 << DOT_VIEWS_CHUNK_LOG2;
+static_assert(DOT_VIEWS_STREAMS == 1 || DOT_VIEWS_STREAMS == 2, "one or two render streams");
+
+// Workspace layout: the cameras in render order, then the ring of chunk buffers (rgb, then T when
+// requested), every part 256-byte aligned.
+struct ViewsPlan {
+    int64_t per_view = 0;     // pixels of one view
+    int32_t chunk_views = 0;  // views of a full chunk (the capacity of a ring buffer)
+    int32_t slots = 0;
+    std::vector<int32_t> first;  // the chunks: first view (in render order) of each, then n
+    int64_t cams_bytes = 0, rgb_bytes = 0, T_bytes = 0, total = 0;
+};
+
+int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
+
+bool plan_views(int32_t n, int32_t W, int32_t H, bool with_T, ViewsPlan &p) {
+    if (n < 0 || n > 65535 || W <= 0 || H <= 0 || W > 65536 || H > 65536) return false;
+    p = ViewsPlan{};
+    p.per_view = (int64_t)W * H;
+    if (n == 0) return true;
+    const int64_t want = std::min<int64_t>(n, std::max<int64_t>(1, (p.per_view * n + kChunkRays - 1) / kChunkRays));
+    p.chunk_views = (int32_t)((n + want - 1) / want);
+    int32_t v = 0;
+    while (n - v > p.chunk_views) {  // full chunks
+        p.first.push_back(v);
+        v += p.chunk_views;
+    }
+    while (v < n) {  // the rest: one chunk, or halving chunks after a full one
+        p.first.push_back(v);
+        const int32_t rem = n - v;
+        v += (DOT_VIEWS_TAPER && v > 0 && rem > 1) ? (rem + 1) / 2 : rem;
+    }
+    p.first.push_back(n);
+    p.slots = std::min<int32_t>(kViewSlots, (int32_t)p.first.size() - 1);
+    p.cams_bytes = align256((int64_t)n * (int64_t)sizeof(dot_camera));
+    p.rgb_bytes = align256(p.chunk_views * p.per_view * 3 * (int64_t)sizeof(float));
+    p.T_bytes = with_T ? align256(p.chunk_views * p.per_view * (int64_t)sizeof(float)) : 0;
+    p.total = p.cams_bytes + p.slots * (p.rgb_bytes + p.T_bytes);
+    return true;
+}
+
+// The streams and per-slot events of one call; on every exit the work already queued finishes
+// before the host buffers and the workspace are handed back.
+struct ViewsPipe {
+    cudaStream_t render[2] = {nullptr, nullptr}, copy = nullptr;
+    bool own_render1 = false;
+    cudaEvent_t ready = nullptr, rendered[kViewSlots] = {}, copied[kViewSlots] = {};
+    ~ViewsPipe() {
+        if (copy) {
+            cudaStreamSynchronize(copy);
+            cudaStreamDestroy(copy);
+        }
+        if (own_render1) {
+            cudaStreamSynchronize(render[1]);
+            cudaStreamDestroy(render[1]);
+        }
+        cudaStreamSynchronize(render[0]);
+        if (ready) cudaEventDestroy(ready);
+        for (int i = 0; i < kViewSlots; i++) {
+            if (rendered[i]) cudaEventDestroy(rendered[i]);
+            if (copied[i]) cudaEventDestroy(copied[i]);
+        }
+    }
+};
+
+// device-to-host copies of `cnt` views of one chunk: view j of the chunk goes to host view
+// order[j]; runs of consecutive views go in one copy
+cudaError_t copy_views_out(float *host, const float *dev, const int32_t *order, int32_t cnt,
+                           int64_t floats_per_view, cudaStream_t s) {
+    const size_t bytes = (size_t)floats_per_view * sizeof(float);
+    for (int32_t j = 0; j < cnt;) {
+        int32_t e = j + 1;
+        while (e < cnt && order[e] == order[e - 1] + 1) e++;
+        cudaError_t err = cudaMemcpyAsync(host + (int64_t)order[j] * floats_per_view,
+                                          dev + (int64_t)j * floats_per_view, bytes * (size_t)(e - j),
+                                          cudaMemcpyDeviceToHost, s);
+        if (err != cudaSuccess) return err;
+        j = e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int64_t dot_render_views_host_workspace(int32_t n_cameras, int32_t width, int32_t height,
+                                                   int32_t with_T) {
+    ViewsPlan p;
+    return plan_views(n_cameras, width, height, with_T != 0, p) ? p.total : -1;
+}
+
+extern "C" int dot_render_views_host(const dot_tree *t, const dot_camera *cameras, int32_t n,
+                                     int32_t width, int32_t height, const int32_t *view_order,
+                                     const dot_render_opts *opts, float *rgb, float *T_final,
+                                     void *workspace, int64_t workspace_bytes, void *stream) {
+    int rc = check_tree(t);
+    if (rc) return rc;
+    ViewsPlan p;
+    if (!plan_views(n, width, height, T_final != nullptr, p))
+        return fail(DOT_ERR_INVALID_ARG, "n_cameras must be in [0, 65535] and width, height in [1, 65536]");
+    dot::RenderParams rp;
+    bool exact = false;
+    if ((rc = make_params(t, opts, rp, exact))) return rc;
+    if (rp.signal_mode != DOT_SIGNAL_NONE)
+        return fail(DOT_ERR_INVALID_ARG, "dot_render_views_host: signal_mode must be NONE");
+    if (n == 0) return DOT_OK;
+    if (!cameras || !rgb) return fail(DOT_ERR_INVALID_ARG, "cameras and rgb are required");
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return fail(DOT_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device buffer");
+    if (workspace_bytes < p.total)
+        return fail(DOT_ERR_INVALID_ARG, "workspace is smaller than dot_render_views_host_workspace");
+    std::vector<int32_t> order((size_t)n);
+    if (view_order) {
+        std::vector<char> seen((size_t)n, 0);
+        for (int32_t i = 0; i < n; i++) {
+            const int32_t v = view_order[i];
+            if (v < 0 || v >= n || seen[(size_t)v])
+                return fail(DOT_ERR_INVALID_ARG, "view_order is not a permutation of 0..n_cameras-1");
+            seen[(size_t)v] = 1;
+            order[(size_t)i] = v;
+        }
+    } else {
+        for (int32_t i = 0; i < n; i++) order[(size_t)i] = i;
+    }
+    std::vector<dot_camera> cams((size_t)n);  // in render order; alive until the call returns
+    for (int32_t i = 0; i < n; i++) cams[(size_t)i] = cameras[order[(size_t)i]];
+
+    char *ws = static_cast<char *>(workspace);
+    dot_camera *d_cams = reinterpret_cast<dot_camera *>(ws);
+    ViewsPipe pipe;
+    pipe.render[0] = pipe.render[1] = S(stream);
+    const char *where = "dot_render_views_host";
+    API_CK(cudaStreamCreateWithFlags(&pipe.copy, cudaStreamNonBlocking), where);
+    API_CK(cudaEventCreateWithFlags(&pipe.ready, cudaEventDisableTiming), where);
+    for (int i = 0; i < p.slots; i++) {
+        API_CK(cudaEventCreateWithFlags(&pipe.rendered[i], cudaEventDisableTiming), where);
+        API_CK(cudaEventCreateWithFlags(&pipe.copied[i], cudaEventDisableTiming), where);
+    }
+    API_CK(cudaMemcpyAsync(d_cams, cams.data(), (size_t)n * sizeof(dot_camera), cudaMemcpyHostToDevice,
+                           pipe.render[0]),
+           where);
+    if (DOT_VIEWS_STREAMS == 2 && p.first.size() > 2) {
+        API_CK(cudaStreamCreateWithFlags(&pipe.render[1], cudaStreamNonBlocking), where);
+        pipe.own_render1 = true;
+        API_CK(cudaEventRecord(pipe.ready, pipe.render[0]), where);  // the cameras have arrived
+        API_CK(cudaStreamWaitEvent(pipe.render[1], pipe.ready, 0), where);
+    }
+    const dot::TreeView tv = view_of(t);
+    const int32_t n_chunks = (int32_t)p.first.size() - 1;
+    for (int32_t k = 0; k < n_chunks; k++) {
+        const int slot = k % p.slots;
+        cudaStream_t rs_k = pipe.render[k & 1];
+        const int32_t first = p.first[(size_t)k];
+        const int32_t cnt = p.first[(size_t)k + 1] - first;
+        float *d_rgb = reinterpret_cast<float *>(ws + p.cams_bytes + slot * (p.rgb_bytes + p.T_bytes));
+        float *d_T = T_final ? reinterpret_cast<float *>(reinterpret_cast<char *>(d_rgb) + p.rgb_bytes) : nullptr;
+        if (k >= p.slots)  // the slot's previous chunk has left for the host
+            API_CK(cudaStreamWaitEvent(rs_k, pipe.copied[slot], 0), where);
+        dot_rays r{};
+        r.kind = DOT_RAYS_CAMERAS;
+        r.n_cameras = cnt;
+        r.cameras = d_cams + first;
+        r.width = width;
+        r.height = height;
+        dot::RaySource rs;
+        int64_t R = 0;
+        if ((rc = make_rays(&r, rs, R))) return rc;
+        dot::RenderIO io{};
+        io.rgb = d_rgb;
+        io.T_final = d_T;
+        io.status = t->status;
+        API_CK(dot::launch_march_fwd(t->a.storage, t->a.sh_degree, exact, tv, rs, rp, io, rs_k), where);
+        API_CK(cudaEventRecord(pipe.rendered[slot], rs_k), where);
+        API_CK(cudaStreamWaitEvent(pipe.copy, pipe.rendered[slot], 0), where);
+        API_CK(copy_views_out(rgb, d_rgb, order.data() + first, cnt, p.per_view * 3, pipe.copy), where);
+        if (T_final)
+            API_CK(copy_views_out(T_final, d_T, order.data() + first, cnt, p.per_view, pipe.copy), where);
+        API_CK(cudaEventRecord(pipe.copied[slot], pipe.copy), where);
+    }
+    API_CK(cudaStreamSynchronize(pipe.copy), where);
+    if (pipe.own_render1) API_CK(cudaStreamSynchronize(pipe.render[1]), where);
+    API_CK(cudaStreamSynchronize(pipe.render[0]), where);
     return DOT_OK;
 }

@@ -42,7 +42,7 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
                 "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize",
                 "dot_rmsprop_step_sparse", "dot_rmsprop_flush", "dot_render_forward_backward_mse",
-                "dot_camera_order")
+                "dot_camera_order", "dot_render_views_host", "dot_render_views_host_workspace")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -182,11 +182,15 @@ def lib() -> ctypes.CDLL:
         "dot_render_forward_backward_mse": [P, ctypes.POINTER(dot_rays), ctypes.POINTER(dot_render_opts),
                                             P, P, P, P, P, P, P, P, P],
         "dot_camera_order": [P, ctypes.c_int32, P],
+        "dot_render_views_host": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                  ctypes.POINTER(dot_render_opts), P, P, P, ctypes.c_int64, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    L.dot_render_views_host_workspace.argtypes = [ctypes.c_int32] * 4
+    L.dot_render_views_host_workspace.restype = ctypes.c_int64
     _lib = L
     return L
 
@@ -427,6 +431,53 @@ def dot_camera_order(cams_host: np.ndarray) -> np.ndarray:
     order = np.zeros(c.shape[0], np.int32)
     _check(lib().dot_camera_order(c.ctypes.data_as(P), c.shape[0], order.ctypes.data_as(P)))
     return order
+
+
+def _host(t, dtype, numel=None, name="tensor"):
+    """A contiguous CPU tensor of `dtype` (and `numel` elements when given); numpy arrays are
+    wrapped without a copy."""
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(t)
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return t
+
+
+def dot_render_views_host_workspace(n_cameras: int, width: int, height: int,
+                                    with_T: bool = False) -> int:
+    """Device workspace bytes dot_render_views_host needs (-1 for invalid sizes)."""
+    return int(lib().dot_render_views_host_workspace(int(n_cameras), int(width), int(height),
+                                                     int(bool(with_T))))
+
+
+def dot_render_views_host(tree: Octree, cams_host, width: int, height: int,
+                          opts: dot_render_opts, rgb_host, T_host=None, view_order=None,
+                          workspace: Optional[torch.Tensor] = None, stream=None):
+    """Whole views from host cameras ([n, 18] float32 records) to host images (float32
+    [n][H][W][3], and [n][H][W] for T_host), chunked with the device-to-host copies overlapping
+    the march (see dot.h).  view_order: host int32 [n] permutation or None; workspace: device
+    uint8 tensor of at least dot_render_views_host_workspace(...) bytes (allocated when None)."""
+    cams = _host(cams_host, torch.float32, name="cameras")
+    if cams.dim() != 2 or cams.shape[1] != 18:
+        raise ValueError("cameras must be [n, 18] float32 records")
+    n = cams.shape[0]
+    R = n * int(width) * int(height)
+    rgb = _host(rgb_host, torch.float32, 3 * R, "rgb")
+    T = _host(T_host, torch.float32, R, "T_final") if T_host is not None else None
+    order = None
+    if view_order is not None:
+        order = _host(view_order, torch.int32, n, "view_order")
+    need = dot_render_views_host_workspace(n, width, height, T is not None)
+    if need < 0:
+        raise ValueError("camera count or resolution out of range")
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+    _need(workspace, torch.uint8, name="workspace")
+    _check(lib().dot_render_views_host(tree.handle, _ptr(cams), n, int(width), int(height),
+                                       _ptr(order), ctypes.byref(opts), _ptr(rgb), _ptr(T),
+                                       _ptr(workspace), workspace.numel(), _stream(stream)))
 
 
 def n_rays_of(r: dot_rays) -> int:

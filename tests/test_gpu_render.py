@@ -201,3 +201,75 @@ def test_view_order_renders_the_same_rays():
     others = [v for v in range(7) if v != skipped]
     assert torch.equal(img[others], a.view(7, -1, 3)[others])
     tree.free()
+
+
+def _forward_all(dot, tree, cam_t, W, H, opts):
+    n = cam_t.shape[0]
+    rgb = torch.empty(n * W * H, 3, device="cuda")
+    T = torch.empty(n * W * H, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, W, H), opts, rgb, T)
+    torch.cuda.synchronize()
+    return rgb.cpu(), T.cpu()
+
+
+def test_views_to_host_match_the_device_forward():
+    """dot_render_views_host (chunks of about 2^23 rays over two render streams, three chunk
+    buffers in a ring, copies on a third stream) writes the same bits as one dot_render_forward
+    launch: 40 views of 800x800 go in seven chunks (10, 10, 10, 5, 3, 1, 1 views), so the ring
+    wraps; with and without a view order and T, into pinned and pageable host buffers; a given
+    workspace is reused."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(21, max_depth=6, sh_degree=3, storage=si.STORAGE_F16, n_prims=5)
+    tree = dot.octree_from_scene(scene)
+    W, H, n = 800, 800, 40
+    cams = [si.pinhole((3 * np.cos(a), 0.5 + 0.3 * np.sin(3 * a), 3 * np.sin(a)), W, H, 700.0)
+            for a in np.linspace(0, 6.2, n)]
+    recs = torch.from_numpy(np.stack([c.packed() for c in cams]).astype(np.float32))
+    opts = dot.render_opts(background=(1, 1, 1))
+    ref, Tref = _forward_all(dot, tree, recs.cuda(), W, H, opts)
+    ref = ref.view(n, H, W, 3)
+    Tref = Tref.view(n, H, W)
+    order = dot.dot.dot_camera_order(recs.numpy())
+    ws = torch.empty(dot.dot.dot_render_views_host_workspace(n, W, H, True), dtype=torch.uint8,
+                     device="cuda")
+    for pinned, view_order, with_T in ((True, order, True), (False, None, False),
+                                       (True, None, True), (False, order, False)):
+        out = torch.full((n, H, W, 3), -1.0, pin_memory=pinned)
+        T = torch.full((n, H, W), -1.0, pin_memory=pinned) if with_T else None
+        dot.dot.dot_render_views_host(tree, recs, W, H, opts, out, T_host=T,
+                                      view_order=view_order, workspace=ws)
+        assert torch.equal(out, ref)
+        if with_T:
+            assert torch.equal(T, Tref)
+    # the application call (pinned output, nearest-neighbour order)
+    from paper_2307_15333_gb300.render import render_views
+    assert torch.equal(render_views(tree, recs, W, H, opts), ref)
+    assert tree.status() == 0
+    tree.free()
+
+
+def test_views_to_host_argument_errors():
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(22, max_depth=4, sh_degree=1, storage=si.STORAGE_F32)
+    tree = dot.octree_from_scene(scene)
+    cams = [si.pinhole((0.0, 0.0, 3.0 + i), 64, 48, 60.0) for i in range(5)]
+    recs = torch.from_numpy(np.stack([c.packed() for c in cams]).astype(np.float32))
+    out = torch.zeros(5, 48, 64, 3)
+    opts = dot.render_opts()
+    for bad in (np.array([0, 1, 2, 3, 3], np.int32), np.array([0, 1, 2, 3, 5], np.int32),
+                np.array([0, 1, 2, 3, -1], np.int32)):
+        with pytest.raises(dot.dot.DotError) as e:
+            dot.dot.dot_render_views_host(tree, recs, 64, 48, opts, out, view_order=bad)
+        assert e.value.code == dot.dot.DOT_ERR_INVALID_ARG and "permutation" in str(e.value)
+    need = dot.dot.dot_render_views_host_workspace(5, 64, 48)
+    small = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dot.dot.DotError) as e:
+        dot.dot.dot_render_views_host(tree, recs, 64, 48, opts, out, workspace=small)
+    assert "workspace" in str(e.value)
+    sig = dot.render_opts(signal_mode=dot.dot.DOT_SIGNAL_MAX_WEIGHT)
+    with pytest.raises(dot.dot.DotError):
+        dot.dot.dot_render_views_host(tree, recs, 64, 48, sig, out)
+    assert (out == 0).all()                            # nothing was rendered or copied
+    # no views: nothing to do
+    dot.dot.dot_render_views_host(tree, recs[:0], 64, 48, opts, torch.zeros(0))
+    tree.free()
