@@ -86,7 +86,10 @@ extern "C" {
 
 typedef struct dot_tree dot_tree;
 
-/* Caller-supplied allocator for the arrays the tree owns.  alloc returns NULL on failure. */
+/* Caller-supplied allocator for the arrays the tree owns.  alloc returns NULL on failure, else a
+ * block of at least `bytes` bytes, 16-byte aligned, usable in stream order on `stream`; a
+ * misaligned block is handed back to free at once and counts as a failed allocation
+ * (DOT_ERR_OOM).  free receives the stream of the call that releases the block. */
 typedef struct {
     void *ctx;
     void *(*alloc)(void *ctx, size_t bytes, void *stream);

@@ -20,10 +20,11 @@ __all__ = ["dot", "DotError", "Octree", "build_desc", "cameras_tensor", "dot_acc
            "select_opts", "octree_from_scene"]
 
 
-def octree_from_scene(scene, stream=None) -> Octree:
+def octree_from_scene(scene, stream=None, allocator=None) -> Octree:
     """Builds the octree of a scene description (any object with center, half_size, max_depth,
-    sh_degree, storage, prims, density_lo/hi, sh_std, sh_dc, seed attributes)."""
+    sh_degree, storage, prims, density_lo/hi, sh_std, sh_dc, seed attributes); `allocator`
+    (dot.TorchAllocator) backs the tree's arrays with torch's caching allocator."""
     d = build_desc(scene.center, scene.half_size, scene.max_depth, scene.sh_degree,
                    scene.storage, scene.prims, (scene.density_lo, scene.density_hi),
                    scene.sh_std, scene.sh_dc, scene.seed)
-    return dot_octree_build(d, stream)
+    return dot_octree_build(d, stream, allocator)

@@ -11,7 +11,14 @@ struct DevAlloc {
     bool has_user = false;
     void *alloc(size_t bytes, cudaStream_t s) const {
         if (bytes == 0) bytes = 16;
-        if (has_user) return user.alloc(user.ctx, bytes, (void *)s);
+        if (has_user) {
+            void *p = user.alloc(user.ctx, bytes, (void *)s);
+            if (p && (reinterpret_cast<uintptr_t>(p) & 15u)) {  // rows are read as 16-byte vectors
+                user.free(user.ctx, p, (void *)s);
+                return nullptr;
+            }
+            return p;
+        }
         void *p = nullptr;
         if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
             cudaGetLastError();

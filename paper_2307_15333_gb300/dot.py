@@ -242,12 +242,45 @@ def _view(ptr: int, shape, dtype: torch.dtype, owner) -> torch.Tensor:
 # ----------------------------------------------------------------------------------------------
 # the tree handle
 # ----------------------------------------------------------------------------------------------
+class TorchAllocator:
+    """A dot_allocator whose blocks come from torch's caching allocator: each block is a uint8
+    CUDA tensor kept alive until the library frees it (stream-ordered through record_stream).
+    ``offset`` shifts every returned pointer by that many bytes inside its tensor (a test hook
+    for the library's alignment check).  Keep the object alive while any tree built with it is."""
+
+    def __init__(self, offset: int = 0):
+        self.offset = int(offset)
+        self.live = {}
+        self.n_alloc = self.n_free = 0
+
+        def _alloc(ctx, nbytes, stream):
+            try:
+                t = torch.empty(int(nbytes) + self.offset, dtype=torch.uint8, device="cuda")
+            except RuntimeError:
+                return None
+            p = t.data_ptr() + self.offset
+            self.live[p] = t
+            self.n_alloc += 1
+            return p
+
+        def _free(ctx, ptr, stream):
+            t = self.live.pop(ptr, None)
+            if t is not None:
+                self.n_free += 1
+                if stream:
+                    t.record_stream(torch.cuda.ExternalStream(stream))
+
+        self._fns = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        self.struct = dot_allocator(None, self._fns[0], self._fns[1])
+
+
 class Octree:
     """Owner of a ``dot_tree`` handle.  ``sigma`` / ``sh`` are zero-copy views of the leaf
     parameters (valid until the next refine or free)."""
 
-    def __init__(self, handle: ctypes.c_void_p):
+    def __init__(self, handle: ctypes.c_void_p, allocator: Optional[TorchAllocator] = None):
         self.handle = handle
+        self.allocator = allocator        # kept alive for the tree's later allocations and frees
 
     @property
     def _as_parameter_(self):
@@ -505,13 +538,15 @@ def dot_last_error() -> str:
     return lib().dot_last_error().decode()
 
 
-def dot_octree_build(desc: dot_build_desc, stream=None) -> Octree:
+def dot_octree_build(desc: dot_build_desc, stream=None,
+                     allocator: Optional[TorchAllocator] = None) -> Octree:
     h = ctypes.c_void_p()
-    _check(lib().dot_octree_build(ctypes.byref(desc), None, _stream(stream), ctypes.byref(h)))
-    return Octree(h)
+    al = ctypes.byref(allocator.struct) if allocator is not None else None
+    _check(lib().dot_octree_build(ctypes.byref(desc), al, _stream(stream), ctypes.byref(h)))
+    return Octree(h, allocator)
 
 
-def dot_tree_import(host: dict, stream=None) -> Octree:
+def dot_tree_import(host: dict, stream=None, allocator: Optional[TorchAllocator] = None) -> Octree:
     """Tree from host arrays (keys child, node_parent, node_key, leaf_parent, leaf_key, sigma,
     sh [L,3,K], center, half_size, sh_degree, storage)."""
     keep = {k: np.ascontiguousarray(host[k]) for k in
@@ -526,8 +561,9 @@ def dot_tree_import(host: dict, stream=None) -> Octree:
     for k, v in keep.items():
         setattr(h, k, v.ctypes.data_as(P))
     out = ctypes.c_void_p()
-    _check(lib().dot_tree_import(ctypes.byref(h), None, _stream(stream), ctypes.byref(out)))
-    return Octree(out)
+    al = ctypes.byref(allocator.struct) if allocator is not None else None
+    _check(lib().dot_tree_import(ctypes.byref(h), al, _stream(stream), ctypes.byref(out)))
+    return Octree(out, allocator)
 
 
 def dot_render_forward(tree: Octree, rays: dot_rays, opts: dot_render_opts, rgb: torch.Tensor,
