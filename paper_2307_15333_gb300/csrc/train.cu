@@ -18,6 +18,14 @@ constexpr int kTrainThreads = 256;
 #ifndef DOT_SPARSE_GROUP
 #define DOT_SPARSE_GROUP 16
 #endif
+// leaves a group updates per pass of the sparse RMSProp step, and the blocks per SM its register
+// budget is built for (0: no bound)
+#ifndef DOT_SPARSE_UNROLL
+#define DOT_SPARSE_UNROLL 2
+#endif
+#ifndef DOT_SPARSE_MINB
+#define DOT_SPARSE_MINB 4
+#endif
 
 // grad[r][c] = 2 (rgb - target) / (3 R); loss_sum += sum (rgb - target)^2 / (3 R)
 __global__ void __launch_bounds__(kTrainThreads)
@@ -154,6 +162,23 @@ int grid_for(int64_t n) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// blocks of kTrainThreads for n threads' worth of work, at most one resident wave of KERNEL
+template <auto KERNEL>
+int resident_grid(int64_t n) {
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, KERNEL, kTrainThreads, 0) != cudaSuccess)
+            cudaGetLastError();
+        return b > 0 ? b : 1;
+    }();
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + kTrainThreads - 1) / kTrainThreads;
+    const int64_t cap = (int64_t)sms * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
 template <typename S>
 cudaError_t rmsprop_array(S *param, int64_t pstride, float *grad, float *ms, int64_t rows,
                           int width, const Rms &o, cudaStream_t s) {
@@ -279,9 +304,11 @@ __device__ __forceinline__ float rho_pow(float rho, int k) {
 }
 
 // G lanes per touched leaf: lane 0 updates the density, the lanes walk the coefficient row four
-// at a time (16-byte gradient and mean-square loads, coalesced across the lanes)
-template <typename S, bool VEC, int G>
-__global__ void __launch_bounds__(kTrainThreads)
+// at a time (16-byte gradient and mean-square loads, coalesced across the lanes).  A group takes U
+// leaves of the list per pass and issues all their loads before any update, so U leaves share
+// one memory round trip.
+template <typename S, bool VEC, int G, int U>
+__global__ void __launch_bounds__(kTrainThreads, DOT_SPARSE_MINB)
 rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
                       S *__restrict__ sigma, S *__restrict__ sh, int row_stride, int width,
                       float *__restrict__ grad_sigma, float *__restrict__ grad_sh,
@@ -294,57 +321,101 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
     const int gl = threadIdx.x & (G - 1);
     const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> LOG_G;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> LOG_G; i < n; i += groups) {
-        const int64_t v = list[i];
-        const float decay = rho_pow(o.rho, step - last[v] - 1);  // the steps it sat out
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> LOG_G; i0 < n;
+         i0 += groups * U) {
+        int32_t v[U];
+        bool ok[U];
+        float decay[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            ok[u] = i0 + u * groups < n;
+            v[u] = ok[u] ? list[i0 + u * groups] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            decay[u] = ok[u] ? rho_pow(o.rho, step - last[v[u]] - 1) : 0.f;  // steps sat out
         if (gl == 0) {
             o.lr = lr_sigma;
-            float m = decay * ms_sigma[v];
-            const float p = rms_update(Storage<S>::to_f32(sigma[v]), grad_sigma[v], m, o);
-            ms_sigma[v] = m;
-            sigma[v] = Storage<S>::from_f32(p);
-            if (o.zero_grad) grad_sigma[v] = 0.f;
+            float ps[U], gs[U], ms[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (ok[u]) {
+                    ps[u] = Storage<S>::to_f32(sigma[v[u]]);
+                    gs[u] = grad_sigma[v[u]];
+                    ms[u] = ms_sigma[v[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (ok[u]) {
+                    float m = decay[u] * ms[u];
+                    const float p = rms_update(ps[u], gs[u], m, o);
+                    ms_sigma[v[u]] = m;
+                    sigma[v[u]] = Storage<S>::from_f32(p);
+                    if (o.zero_grad) grad_sigma[v[u]] = 0.f;
+                }
+            }
         }
         o.lr = lr_sh;
         if constexpr (VEC) {
             using V = Vec4<S>;
             const int q4 = width / 4;
-            float4 *g4 = reinterpret_cast<float4 *>(grad_sh + v * width);
-            float4 *m4 = reinterpret_cast<float4 *>(ms_sh + v * width);
             for (int q = gl; q < q4; q += G) {
-                typename V::T *pv = reinterpret_cast<typename V::T *>(sh + v * row_stride + 4 * q);
-                const float4 g = g4[q];
-                float4 m = m4[q];
-                m.x *= decay;
-                m.y *= decay;
-                m.z *= decay;
-                m.w *= decay;
-                float p[4];
-                V::get(*pv, p);
-                p[0] = rms_update(p[0], g.x, m.x, o);
-                p[1] = rms_update(p[1], g.y, m.y, o);
-                p[2] = rms_update(p[2], g.z, m.z, o);
-                p[3] = rms_update(p[3], g.w, m.w, o);
-                m4[q] = m;
-                *pv = V::make(p);
-                if (o.zero_grad) g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 g[U], m[U];
+                typename V::T pv[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    if (ok[u]) {
+                        g[u] = reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width)[q];
+                        m[u] = reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width)[q];
+                        pv[u] = *reinterpret_cast<const typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    if (!ok[u]) continue;
+                    float4 mm = m[u];
+                    mm.x *= decay[u];
+                    mm.y *= decay[u];
+                    mm.z *= decay[u];
+                    mm.w *= decay[u];
+                    float p[4];
+                    V::get(pv[u], p);
+                    p[0] = rms_update(p[0], g[u].x, mm.x, o);
+                    p[1] = rms_update(p[1], g[u].y, mm.y, o);
+                    p[2] = rms_update(p[2], g[u].z, mm.z, o);
+                    p[3] = rms_update(p[3], g[u].w, mm.w, o);
+                    reinterpret_cast<float4 *>(ms_sh + (int64_t)v[u] * width)[q] = mm;
+                    *reinterpret_cast<typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q) = V::make(p);
+                    if (o.zero_grad)
+                        reinterpret_cast<float4 *>(grad_sh + (int64_t)v[u] * width)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
         } else {
-            for (int c = gl; c < width; c += G) {
-                float *g = grad_sh + v * width + c;
-                float *ms = ms_sh + v * width + c;
-                S *pp = sh + v * row_stride + c;
-                float m = decay * *ms;
-                const float p = rms_update(Storage<S>::to_f32(*pp), *g, m, o);
-                *ms = m;
-                *pp = Storage<S>::from_f32(p);
-                if (o.zero_grad) *g = 0.f;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (!ok[u]) continue;
+                for (int c = gl; c < width; c += G) {
+                    float *g = grad_sh + (int64_t)v[u] * width + c;
+                    float *ms = ms_sh + (int64_t)v[u] * width + c;
+                    S *pp = sh + (int64_t)v[u] * row_stride + c;
+                    float m = decay[u] * *ms;
+                    const float p = rms_update(Storage<S>::to_f32(*pp), *g, m, o);
+                    *ms = m;
+                    *pp = Storage<S>::from_f32(p);
+                    if (o.zero_grad) *g = 0.f;
+                }
             }
         }
         __syncwarp(gmask);  // every lane has read last[v]
         if (gl == 0) {
-            touched[v] = 0;
-            last[v] = step;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (ok[u]) {
+                    touched[v[u]] = 0;
+                    last[v[u]] = step;
+                }
+            }
         }
     }
 }
@@ -403,16 +474,19 @@ cudaError_t launch_rmsprop_sparse(int storage, void *sigma, void *sh, int64_t L,
                      (reinterpret_cast<uintptr_t>(grad_sh) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(ms_sh) & 15) == 0;
     constexpr int G = DOT_SPARSE_GROUP;
-    const int grid = grid_for(L * G);
+    constexpr int U = DOT_SPARSE_UNROLL;
+    // one resident wave: the list length is known only on the device
 #define DOT_SPARSE_LAUNCH(T)                                                                     \
     if (vec)                                                                                     \
-        rmsprop_sparse_kernel<T, true, G><<<grid, kTrainThreads, 0, s>>>(                        \
-            work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh, ms_sigma,  \
-            ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);                               \
+        rmsprop_sparse_kernel<T, true, G, U>                                                     \
+            <<<resident_grid<rmsprop_sparse_kernel<T, true, G, U>>(L * G), kTrainThreads, 0, s>>>( \
+                work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh,        \
+                ms_sigma, ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);                 \
     else                                                                                         \
-        rmsprop_sparse_kernel<T, false, G><<<grid, kTrainThreads, 0, s>>>(                       \
-            work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh, ms_sigma,  \
-            ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);
+        rmsprop_sparse_kernel<T, false, G, U>                                                    \
+            <<<resident_grid<rmsprop_sparse_kernel<T, false, G, U>>(L * G), kTrainThreads, 0, s>>>( \
+                work, count, (T *)sigma, (T *)sh, row_stride, width, grad_sigma, grad_sh,        \
+                ms_sigma, ms_sh, touched, last, step, op.lr_sigma, op.lr_sh, o);
     switch (storage) {
         case DOT_STORAGE_F32: DOT_SPARSE_LAUNCH(float) break;
         case DOT_STORAGE_F16: DOT_SPARSE_LAUNCH(__half) break;
