@@ -542,6 +542,7 @@ def run_dot(args):
     dot.dot_accumulate_signal(tree, rays, opts, dot.dot.DOT_SIGNAL_MAX_WEIGHT, touched)
     u_leaf = int(torch.count_nonzero(touched))
     del touched
+    n_empty = int((tree.sigma <= 0).sum())
 
     # ---- forward + backward on 2^16-ray batches (fixed synthetic dL/dC) ----
     nb = 8
@@ -683,6 +684,13 @@ def run_dot(args):
                              "ray_output_B": 12},
                 "segments_per_ray": seg / R, "occupied_per_ray": occ / R,
                 "occupied_leaves_touched": u_leaf}
+    # compulsory bytes: what one launch must move at least once from HBM
+    compulsory = u_leaf * P + tree.n_nodes * 32 + n_empty * bs + R * 12
+    roofline["compulsory"] = {
+        "bytes": compulsory,
+        "what": "distinct occupied leaves x payload + every node row + every empty density "
+                "+ 12 B per ray",
+        "t_at_peak_ms": compulsory / (hbm * 1e9) * 1e3, "t_meas_ms": mean_launch_s * 1e3}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
