@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdot.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "build.cu", "scan.cu", "select.cu", "refine.cu", "render_fwd.cu",
+SOURCES = ["api.cu", "build.cu", "ropes.cu", "scan.cu", "select.cu", "refine.cu", "render_fwd.cu",
            "render_bwd.cu", "render_signal.cu", "select_noalloc.cu", "render_slots.cu", "train.cu",
            "compress.cu", "canon.cu", "render_fwd_comp.cu", "render_fwdbwd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -134,6 +134,7 @@ dot::TreeView view_of(const dot_tree *t) {
     tv.sigma = t->a.sigma;
     tv.sh = t->a.leaf_rec ? t->a.palette : t->a.sh;
     tv.rec = t->a.leaf_rec;
+    tv.rope = t->a.rope;
     tv.n_nodes = t->a.n_nodes;
     tv.n_leaves = t->a.n_leaves;
     tv.row_stride = t->a.row_stride;
@@ -409,6 +410,7 @@ int dot_tree_import(const dot_host_tree *h, const dot_allocator *alloc, void *st
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(t->a.sh, (size_t)t->a.row_stride * sb, h->sh, 3 * t->a.K * sb,
                               3 * t->a.K * sb, (size_t)L, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = dot::build_ropes(t->a, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         int r = cuda_fail(e, "dot_tree_import");

@@ -304,6 +304,7 @@ cudaError_t build_tree(const dot_build_desc &desc, TreeArrays &out, const DevAll
         }
         DOT_CK(cudaGetLastError());
     }
+    DOT_CK(build_ropes(out, s));
     if (inside_all) DOT_CK(cudaFreeAsync(inside_all, s));
     return cudaSuccess;
 }

@@ -136,6 +136,7 @@ cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevA
     nw.leaf_parent = (int32_t *)alloc.alloc((size_t)L * 4, s);
     nw.leaf_key = (uint64_t *)alloc.alloc((size_t)L * 8, s);
     nw.sigma = alloc.alloc((size_t)L * sb, s);
+    nw.rope = (int2 *)alloc.alloc((size_t)L * 6 * sizeof(int2), s);
     if (old.sh) nw.sh = alloc.alloc((size_t)L * row_bytes, s);
     if (old.leaf_rec) {
         nw.leaf_rec = (uint32_t *)alloc.alloc((size_t)L * 4, s);
@@ -143,7 +144,8 @@ cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevA
     }
     owned_new = true;
     if (!nw.child || !nw.node_parent || !nw.node_key || !nw.leaf_parent || !nw.leaf_key ||
-        !nw.sigma || (old.sh && !nw.sh) || (old.leaf_rec && (!nw.leaf_rec || !nw.palette))) {
+        !nw.sigma || !nw.rope || (old.sh && !nw.sh) ||
+        (old.leaf_rec && (!nw.leaf_rec || !nw.palette))) {
         cleanup();
         return cudaErrorMemoryAllocation;
     }
@@ -222,6 +224,7 @@ cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevA
     if (old.leaf_rec)
         CN_CK(cudaMemcpyAsync(nw.palette, old.palette, ((size_t)1 << old.palette_bits) * row_bytes,
                               cudaMemcpyDeviceToDevice, s));
+    CN_CK(build_ropes(nw, s));
     if (cur) CN_CK(cudaFreeAsync(cur, s));
     if (cur_parent) CN_CK(cudaFreeAsync(cur_parent, s));
     CN_CK(cudaFreeAsync(total, s));

@@ -26,6 +26,7 @@ struct TreeView {
     const void *sigma;
     const void *sh;            // SH rows, or the palette rows of a compressed tree
     const uint32_t *rec;       // compressed tree: per-leaf (density bits | palette row << 16)
+    const int2 *rope;          // [L][6] face neighbours: (node or leaf code, level)
     int64_t n_nodes, n_leaves;
     int32_t row_stride;        // storage elements per SH row
     int32_t max_level;

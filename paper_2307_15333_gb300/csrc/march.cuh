@@ -3,9 +3,10 @@
 //
 // Per ray (Sec. 3 Preliminaries; Eq. 1-2):
 //   1. slab test against the root cube, entry t0 >= 0;
-//   2. the current cell is kept as integer coordinates g on the 2^16 grid; the leaf holding g is
-//      found by descending child pointers, restarting from the deepest common ancestor of the
-//      previous leaf (kept in a per-thread path stack in shared memory);
+//   2. the current cell is kept as integer coordinates g on the 2^16 grid; a step that leaves a
+//      leaf through one face follows that face's rope (the neighbour at the leaf's level, or the
+//      coarser leaf there) and descends from it only if the neighbour is subdivided finer; a step
+//      across an edge or a corner descends from the root;
 //   3. the leaf's exit time is the nearest of its three exit faces; delta = t_exit - t;
 //   4. occupied segments (sigma > 0) are shaded: SH colour, alpha = 1 - exp(-sigma delta),
 //      w = T alpha, C += w c, T *= exp(-sigma delta); the march stops once T < eps_T;
@@ -187,16 +188,14 @@ struct RayOut {
     unsigned long long st[4];  // STATS: hit, steps, occupied, child loads
 };
 
-// NT: threads of the block (stride of the shared path stack).  DEFER: shade each occupied
-// segment one occupied segment later, after prefetching its SH row into L1, so that the row's
-// latency overlaps the traversal in between (a gain for launches too small to hide latency by
-// occupancy).  COMP: the tree is compressed -- density and palette row come from one 32-bit
-// record per leaf and the rows are palette rows.
-template <typename S, int K, int MODE, bool EXACT, int NT = kMarchThreads, bool DEFER = false,
-          bool COMP = false>
+// DEFER: shade each occupied segment one occupied segment later, after prefetching its SH row
+// into L1, so that the row's latency overlaps the traversal in between (a gain for launches too
+// small to hide latency by occupancy).  COMP: the tree is compressed -- density and palette row
+// come from one 32-bit record per leaf and the rows are palette rows.
+template <typename S, int K, int MODE, bool EXACT, bool DEFER = false, bool COMP = false>
 __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams &rp,
                                           const RenderIO &io, int64_t ray, const float ow[3],
-                                          const float dw[3], int32_t *stack, RayOut &out) {
+                                          const float dw[3], RayOut &out) {
     using PT = typename std::conditional<EXACT, FF, float>::type;
     RayAxes r;
 #pragma unroll
@@ -284,14 +283,13 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     const S *sigma = reinterpret_cast<const S *>(tv.sigma);
     const S *shp = reinterpret_cast<const S *>(tv.sh);
 
-    // descend from (node, level) to the leaf holding gc, recording the path on the stack
+    // descend from (node, level) to the leaf holding gc
     auto descend = [&](int32_t node, int level, int32_t &leaf_out, int &level_out) -> bool {
         int32_t c;
         const int g0 = gc[0] << 2, g1 = gc[1] << 1, g2 = gc[2];  // slot bits land at 4, 2, 1
         while (true) {
             const int sh = kGridBits - 1 - level;
             const int j = ((g0 >> sh) & 4) | ((g1 >> sh) & 2) | ((g2 >> sh) & 1);
-            stack[level * NT] = node;
             c = __ldg(tv.child + (int64_t)node * 8 + j);
             ++level;
             if constexpr (MODE == kStats) out.st[3] += 1;
@@ -428,12 +426,16 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
 
         // ---- next cell and its leaf ----
         const float toutv = val(tout);
+        int crossed = 0, face = 0;  // faces crossed at tout; the last one (2 axis + upper)
         if constexpr (!EXACT) {
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (te[a] == tout) {  // step across every face hit at tout
-                    gc[a] = r.inv16[a] > 0.f ? lo_g[a] + cs : lo_g[a] - 1;
+                    const bool up = r.inv16[a] > 0.f;
+                    gc[a] = up ? lo_g[a] + cs : lo_g[a] - 1;
                     outside |= (unsigned)gc[a] > 65535u;
+                    ++crossed;
+                    face = 2 * a + (up ? 1 : 0);
                 } else {              // the exit point, clamped into the old cell
                     const int gi = (int)floorf(fmaf(toutv, r.dn16[a], r.on16[a]));
                     gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
@@ -445,6 +447,8 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
                 if (r.sg[a] != 0 && eq(te[a], tout)) {
                     gc[a] = r.sg[a] > 0 ? lo_g[a] + cs : lo_g[a] - 1;
                     outside |= (gc[a] < 0) | (gc[a] > 65535);
+                    ++crossed;
+                    face = 2 * a + (r.sg[a] > 0 ? 1 : 0);
                 } else {
                     const float p = fmaf(toutv, r.dn[a], r.on[a]);
                     const int gi = (int)floorf(p * 65536.f);
@@ -455,9 +459,23 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         int32_t next_leaf = 0;
         int next_level = -1;
         if (!outside) {
-            const unsigned dbits = (unsigned)((gc[0] ^ lo_g[0]) | (gc[1] ^ lo_g[1]) | (gc[2] ^ lo_g[2]));
-            const int lca = kGridBits - 1 - (31 - __clz(dbits));
-            if (!descend(stack[lca * NT], lca, next_leaf, next_level)) {
+            bool found;
+            if (crossed == 1) {  // across one face: its rope
+                const int2 rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
+                if constexpr (MODE == kStats) out.st[3] += 1;
+                if (rp.x < 0 ? (int64_t)(-1 - (int64_t)rp.x) >= tv.n_leaves : rp.x >= tv.n_nodes) {
+                    found = false;  // not a node or leaf of this tree (or outside: contradicts gc)
+                } else if (rp.x < 0) {
+                    next_leaf = -1 - rp.x;
+                    next_level = rp.y;
+                    found = true;
+                } else {
+                    found = descend(rp.x, rp.y, next_leaf, next_level);
+                }
+            } else {  // across an edge or a corner: from the root
+                found = descend(0, 0, next_leaf, next_level);
+            }
+            if (!found) {
                 atomicOr(io.status, DOT_STATUS_STEP_LIMIT);
                 next_level = -1;
             }
@@ -566,8 +584,6 @@ template <typename S, int K, int MODE, bool EXACT, int MINB, int NT = kMarchThre
           bool DEFER = false, bool COMP = false>
 __global__ void __launch_bounds__(NT, MINB)
 march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
-    __shared__ int32_t s_stack[kMaxLevels * NT];
-    int32_t *stack = s_stack + threadIdx.x;
 
     int64_t ray;
     bool valid;
@@ -610,7 +626,7 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
                 out.rgbf[ch] = __ldg(io.rgb_fwd + 3 * ray + ch);
             }
         }
-        march_ray<S, K, MODE, EXACT, NT, DEFER, COMP>(tv, rp, io, ray, ow, dw, stack, out);
+        march_ray<S, K, MODE, EXACT, DEFER, COMP>(tv, rp, io, ray, ow, dw, out);
         if constexpr (MODE == kFwd || MODE == kFwdBwd) {
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) io.rgb[3 * ray + ch] = out.rgb[ch];
@@ -630,7 +646,7 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
                 rb.signal_mode = DOT_SIGNAL_NONE;
                 RenderIO ib = io;
                 ib.signal = nullptr;
-                march_ray<S, K, kBwd, EXACT, NT, DEFER, COMP>(tv, rb, ib, ray, ow, dw, stack, b);
+                march_ray<S, K, kBwd, EXACT, DEFER, COMP>(tv, rb, ib, ray, ow, dw, b);
             }
         }
     }

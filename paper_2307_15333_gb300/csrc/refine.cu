@@ -310,6 +310,7 @@ cudaError_t refine_tree(const TreeArrays &old, const uint8_t *prune, const uint8
         default: launch_apply<__nv_bfloat16>(old, R, nw, leaf_map, s); break;
     }
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = build_ropes(nw, s);
     for (int i = 0; e == cudaSuccess && i < n_aux; i++) {
         if (nw.n_leaves == 0) break;
         remap_aux_kernel<<<(unsigned)((nw.n_leaves + 255) / 256), 256, 0, s>>>(

@@ -29,9 +29,7 @@ template <typename S, int K, bool EXACT, bool COMP>
 __global__ void __launch_bounds__(kSlotThreads, 8)
 slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots, RenderParams rp,
              unsigned long long *__restrict__ counter, uint32_t *status) {
-    __shared__ int32_t s_stack[kMaxLevels * kSlotThreads];
     __shared__ long long s_tile;
-    int32_t *stack = s_stack + threadIdx.x;
     const SlotHeader *hdr = reinterpret_cast<const SlotHeader *>(table);
     const dot_slot *slots = reinterpret_cast<const dot_slot *>(table + sizeof(SlotHeader));
     const int n = min(hdr->n_slots, max_slots);
@@ -66,8 +64,7 @@ slots_kernel(SlotTrees trees, const char *__restrict__ table, int32_t max_slots,
             float ow[3], dw[3];
             camera_ray(&sl->camera, px, py, ow, dw);
             RayOut out;
-            march_ray<S, K, kFwd, EXACT, kSlotThreads, false, COMP>(trees.t[tr], rp, io, 0, ow,
-                                                                     dw, stack, out);
+            march_ray<S, K, kFwd, EXACT, false, COMP>(trees.t[tr], rp, io, 0, ow, dw, out);
             float *dst = sl->out + ((int64_t)py * W + px) * 3;
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) dst[ch] = out.rgb[ch];

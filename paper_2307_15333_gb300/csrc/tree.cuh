@@ -48,6 +48,9 @@ struct TreeArrays {
     void *palette = nullptr;
     uint32_t *leaf_rec = nullptr;
     int palette_bits = 0;
+    // ropes [L][6]: across face 2 axis + upper of a leaf, (node id at the leaf's level or leaf
+    // code -1 - v, its level), or (INT32_MIN, 0) outside the root; built by build_ropes
+    int2 *rope = nullptr;
 };
 
 inline void free_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStream_t s) {
@@ -60,8 +63,10 @@ inline void free_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStream_t s) 
     al.release(a.sh, s);
     al.release(a.palette, s);
     al.release(a.leaf_rec, s);
+    al.release(a.rope, s);
     a.palette = nullptr;
     a.leaf_rec = nullptr;
+    a.rope = nullptr;
     a.palette_bits = 0;
     a.child = a.node_parent = a.leaf_parent = nullptr;
     a.node_key = a.leaf_key = nullptr;
@@ -78,8 +83,9 @@ inline cudaError_t alloc_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStre
     a.leaf_key = (uint64_t *)al.alloc((size_t)a.n_leaves * sizeof(uint64_t), s);
     a.sigma = al.alloc((size_t)a.n_leaves * sb, s);
     a.sh = al.alloc((size_t)a.n_leaves * (size_t)a.row_stride * sb, s);
+    a.rope = (int2 *)al.alloc((size_t)a.n_leaves * 6 * sizeof(int2), s);
     if (!a.child || !a.node_parent || !a.node_key || !a.leaf_parent || !a.leaf_key || !a.sigma ||
-        !a.sh) {
+        !a.sh || !a.rope) {
         free_tree_arrays(a, al, s);
         return cudaErrorMemoryAllocation;
     }
@@ -88,6 +94,9 @@ inline cudaError_t alloc_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStre
 
 cudaError_t build_tree(const dot_build_desc &desc, TreeArrays &out, const DevAlloc &alloc,
                        cudaStream_t s);
+
+// ropes.cu: fills a.rope from a.child and a.leaf_key (after every change of the structure)
+cudaError_t build_ropes(const TreeArrays &a, cudaStream_t s);
 
 struct RefinePlan {
     int64_t n_nodes, n_leaves, n_merged, n_sampled, n_capped, n_survive, n_keep;
