@@ -269,6 +269,38 @@ def alg_bytes_of(stats, n_rays, storage_bytes, K):
     return occ * P + (seg - occ) * storage_bytes + seg * 4 + n_rays * 12
 
 
+def grad_bytes_per_occupied(K):
+    """FP32 gradient update of one occupied segment: dL/dsigma and the 3K SH gradients."""
+    return 4 * (1 + 3 * K)
+
+
+def alg_bytes_bwd(stats, n_rays, storage_bytes, K):
+    """Algorithmic bytes of one backward launch (the march recomputed): the forward's leaf and
+    node reads, the gradient update of every occupied segment, and dL/dC and C of every ray."""
+    return (alg_bytes_of(stats, n_rays, storage_bytes, K) - n_rays * 12
+            + stats["occupied"] * grad_bytes_per_occupied(K) + n_rays * 24)
+
+
+def alg_bytes_fused(stats, n_rays, storage_bytes, K):
+    """Algorithmic bytes of one fused training pass: the forward's leaf and node reads, the
+    gradient update of every occupied segment, and per ray the target read and C and dL/dC
+    written."""
+    return (alg_bytes_of(stats, n_rays, storage_bytes, K) - n_rays * 12
+            + stats["occupied"] * grad_bytes_per_occupied(K) + n_rays * 36)
+
+
+def sum_stats(tree, rays_list, opts):
+    """Segment counts summed over several ray sets (counting passes, not timed)."""
+    from paper_2307_15333_gb300 import dot as d
+    tot = {"segments": 0, "occupied": 0, "rays": 0}
+    for r in rays_list:
+        st = d.dot_render_stats(tree, r, opts)
+        tot["segments"] += st["segments"]
+        tot["occupied"] += st["occupied"]
+        tot["rays"] += d.n_rays_of(r)
+    return tot
+
+
 def timed(fn, n, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -422,6 +454,19 @@ def measure_tanks_temples(steps: int):
         pair(i)
     torch.cuda.synchronize()
     pms = timed(pair, 100, stream)
+    bst = sum_stats(tree, batches, opts)
+    b_pair = (alg_bytes_of(bst, bst["rays"], 2, K) + alg_bytes_bwd(bst, bst["rays"], 2, K)) / 8
+    # forward + backward over all 150 views in one batch (311 M rays per pair)
+    gfull = torch.full((R, 3), 1e-6, device="cuda")
+    dot.dot_render_forward(tree, rays, opts, rgb)
+    dot.dot_render_backward(tree, rays, opts, gfull, rgb, gs, gsh)
+    torch.cuda.synchronize()
+    fpairs = 2
+    fms = timed(lambda i: (dot.dot_render_forward(tree, rays, opts, rgb),
+                           dot.dot_render_backward(tree, rays, opts, gfull, rgb, gs, gsh)),
+                fpairs, stream)
+    del gfull
+    f_pair = ab + alg_bytes_bwd(st, R, 2, K)
     out = {"workload": "tanks_temples_d10_sh3_bf16_150x1920x1080", "leaves": L,
            "nodes": tree.n_nodes, "rays_per_step": R,
            "fwd": {"value": R * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms / n,
@@ -429,7 +474,12 @@ def measure_tanks_temples(steps: int):
                    "alg_bytes_per_launch": ab, "segments_per_ray": st["segments"] / R,
                    "occupied_per_ray": st["occupied"] / R},
            "fwd_bwd": {"value": BATCH * 100 / (pms / 1e3) / 1e6, "unit": "Mrays/s",
-                       "batch_rays": BATCH, "ms_per_pair": pms / 100}}
+                       "batch_rays": BATCH, "ms_per_pair": pms / 100, "alg_bytes_per_pair": b_pair,
+                       "roofline_frac": b_pair / (pms / 100 / 1e3) / 1e9 / hbm},
+           "fwd_bwd_full_batch": {"value": R * fpairs / (fms / 1e3) / 1e6, "unit": "Mrays/s",
+                                  "batch_rays": R, "ms_per_pair": fms / fpairs,
+                                  "alg_bytes_per_pair": f_pair,
+                                  "roofline_frac": f_pair / (fms / fpairs / 1e3) / 1e9 / hbm}}
     tree.free()
     return out
 
@@ -572,9 +622,14 @@ def run_dot(args):
     torch.cuda.synchronize()
     clk2 = clocks2.stop()
     fb_ms = max_over_ranks(e0.elapsed_time(e1))
+    bst = sum_stats(tree, batches, opts)                  # the nb batches (counting pass)
+    b_pair = (alg_bytes_of(bst, bst["rays"], bs, K) + alg_bytes_bwd(bst, bst["rays"], bs, K)) / nb
+    b_fused = alg_bytes_fused(bst, bst["rays"], bs, K) / nb
     fwd_bwd = {"value": BATCH * pairs * ws / (fb_ms / 1e3) / 1e6, "unit": "Mrays/s",
                "batch_rays": BATCH, "pairs": pairs, "ms_per_pair": fb_ms / pairs,
                "grad": "fixed synthetic dL/dC; FP32 gradients accumulate across pairs",
+               "alg_bytes_per_pair": b_pair,
+               "roofline_frac": b_pair / (fb_ms / pairs / 1e3) / 1e9 / peaks()[0],
                "clocks": clk2}
 
     # ---- the same batches through the fused training pass (forward, MSE gradient and backward
@@ -592,7 +647,9 @@ def run_dot(args):
     fu_ms = max_over_ranks(e0.elapsed_time(e1))
     fwd_bwd["fused_mse"] = {"value": BATCH * pairs * ws / (fu_ms / 1e3) / 1e6, "unit": "Mrays/s",
                             "batch_rays": BATCH, "passes": pairs, "ms_per_pass": fu_ms / pairs,
-                            "pass": "forward + MSE gradient + backward in one launch"}
+                            "pass": "forward + MSE gradient + backward in one launch",
+                            "alg_bytes_per_pass": b_fused,
+                            "roofline_frac": b_fused / (fu_ms / pairs / 1e3) / 1e9 / peaks()[0]}
     del tgt, gfused
 
     # ---- forward + backward over all views in one batch (64 M rays per pair) ----
@@ -609,9 +666,11 @@ def run_dot(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ff_ms = max_over_ranks(e0.elapsed_time(e1))
+    f_pair = alg_bytes + alg_bytes_bwd(st, R, bs, K)
     fwd_bwd["full_batch"] = {"value": R * full_pairs * ws / (ff_ms / 1e3) / 1e6,
                              "unit": "Mrays/s", "batch_rays": R, "pairs": full_pairs,
-                             "ms_per_pair": ff_ms / full_pairs}
+                             "ms_per_pair": ff_ms / full_pairs, "alg_bytes_per_pair": f_pair,
+                             "roofline_frac": f_pair / (ff_ms / full_pairs / 1e3) / 1e9 / peaks()[0]}
     del gfull
 
     # ---- end to end through host buffers (pinned cameras in, pinned images out) ----
