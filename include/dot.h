@@ -19,9 +19,10 @@
  *    caller's dot_allocator when one is given, else with cudaMallocAsync on the call's stream.
  *  - Anomalies seen inside kernels (a ray exceeding the step cap) set bits of a per-tree device
  *    status word, read and cleared by dot_tree_status().
- *  - Besides the arrays of dot_tree_info, a tree keeps a face-neighbour table (48 bytes per
+ *  - Besides the arrays of dot_tree_info, a tree keeps a face-neighbour table (24 bytes per
  *    leaf) that the renders follow from leaf to leaf; every call that changes the structure
- *    rebuilds it.
+ *    rebuilds it.  A tree holds at most 2^27 leaves: a build, import, refine or renumbering that
+ *    would exceed that fails with DOT_ERR_UNSUPPORTED.
  *
  * Geometry
  *  - The root cube is [c - h, c + h]^3 (world units).  A cell at level l (root = 0) with

@@ -60,6 +60,10 @@ int fail(int code, const std::string &msg) {
 
 int cuda_fail(cudaError_t e, const char *where) {
     cudaGetLastError();
+    if (e == cudaErrorNotSupported) {  // the library's own capacity limits
+        g_err = std::string(where) + ": the tree would exceed 2^27 leaves";
+        return DOT_ERR_UNSUPPORTED;
+    }
     g_err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return e == cudaErrorMemoryAllocation ? DOT_ERR_OOM : DOT_ERR_CUDA;
 }

@@ -136,7 +136,7 @@ cudaError_t canonicalize_tree(const TreeArrays &old, TreeArrays *out, const DevA
     nw.leaf_parent = (int32_t *)alloc.alloc((size_t)L * 4, s);
     nw.leaf_key = (uint64_t *)alloc.alloc((size_t)L * 8, s);
     nw.sigma = alloc.alloc((size_t)L * sb, s);
-    nw.rope = (int2 *)alloc.alloc((size_t)L * 6 * sizeof(int2), s);
+    nw.rope = (int32_t *)alloc.alloc((size_t)L * 6 * sizeof(int32_t), s);
     if (old.sh) nw.sh = alloc.alloc((size_t)L * row_bytes, s);
     if (old.leaf_rec) {
         nw.leaf_rec = (uint32_t *)alloc.alloc((size_t)L * 4, s);

@@ -13,8 +13,13 @@
 namespace dot {
 
 constexpr int kGridBits = 16;              // finest addressable level: cells of 2^-16 root edge
+constexpr int kRopeLevelBits = 4;          // a rope to a leaf holds its id and level difference
+constexpr int64_t kMaxRopeLeaves = (int64_t)1 << (31 - kRopeLevelBits);  // leaves a tree may hold
 constexpr int kMaxLevels = 16;
-constexpr int kMarchThreads = 256;         // threads per march block (16 x 16 pixel tile)
+#ifndef DOT_SMALL_NT
+#define DOT_SMALL_NT 256
+#endif
+constexpr int kMarchThreads = DOT_SMALL_NT;  // threads per block of launches below two waves
 constexpr int kMaxPrimitives = 4096;
 
 // ---------------------------------------------------------------------------------------------
@@ -26,7 +31,7 @@ struct TreeView {
     const void *sigma;
     const void *sh;            // SH rows, or the palette rows of a compressed tree
     const uint32_t *rec;       // compressed tree: per-leaf (density bits | palette row << 16)
-    const int2 *rope;          // [L][6] face neighbours: (node or leaf code, level)
+    const int32_t *rope;       // [L][6] face neighbours (see ropes.cu)
     int64_t n_nodes, n_leaves;
     int32_t row_stride;        // storage elements per SH row
     int32_t max_level;

@@ -461,16 +461,15 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (!outside) {
             bool found;
             if (crossed == 1) {  // across one face: its rope
-                const int2 rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
+                const int32_t rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
                 if constexpr (MODE == kStats) out.st[3] += 1;
-                if (rp.x < 0 ? (int64_t)(-1 - (int64_t)rp.x) >= tv.n_leaves : rp.x >= tv.n_nodes) {
-                    found = false;  // not a node or leaf of this tree (or outside: contradicts gc)
-                } else if (rp.x < 0) {
-                    next_leaf = -1 - rp.x;
-                    next_level = rp.y;
-                    found = true;
-                } else {
-                    found = descend(rp.x, rp.y, next_leaf, next_level);
+                if (rp >= 0) {  // the node at this leaf's level: descend into the finer neighbour
+                    found = rp < tv.n_nodes && descend(rp, level, next_leaf, next_level);
+                } else {        // a leaf at this level or coarser (INT32_MIN, outside, fails here)
+                    const int32_t code = -1 - rp;
+                    next_leaf = code >> kRopeLevelBits;
+                    next_level = level - (code & ((1 << kRopeLevelBits) - 1));
+                    found = next_leaf < tv.n_leaves && rp != INT32_MIN;
                 }
             } else {  // across an edge or a corner: from the root
                 found = descend(0, 0, next_leaf, next_level);

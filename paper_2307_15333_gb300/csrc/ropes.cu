@@ -13,7 +13,7 @@ namespace {
 
 // one thread per (leaf, face); face f = 2 axis + (1 for the upper face)
 __global__ void ropes_kernel(const int32_t *__restrict__ child, const uint64_t *__restrict__ leaf_key,
-                             int64_t L, int2 *__restrict__ rope) {
+                             int64_t L, int32_t *__restrict__ rope) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 6 * L) return;
     const int64_t v = i / 6;
@@ -33,15 +33,19 @@ __global__ void ropes_kernel(const int32_t *__restrict__ child, const uint64_t *
 #pragma unroll
     for (int a = 0; a < 3; a++) g[a] = c[a] << (kGridBits - level);  // corner on the 2^16 grid
     g[axis] += (f & 1) ? cs : -cs;                                   // the neighbour's corner
-    int2 out = make_int2(INT32_MIN, 0);                              // outside the root
+    int32_t out = INT32_MIN;                                         // outside the root
     if (g[axis] >= 0 && g[axis] < (1 << kGridBits)) {
         int32_t node = 0;
         for (int l = 0; l < level; l++) {
             const int sh = kGridBits - 1 - l;
             const int j = (((g[0] >> sh) & 1) << 2) | (((g[1] >> sh) & 1) << 1) | ((g[2] >> sh) & 1);
             const int32_t ch = child[(int64_t)node * 8 + j];
-            if (ch < 0 || l + 1 == level) {  // a leaf at level l + 1, or the node at the leaf's level
-                out = make_int2(ch, l + 1);
+            if (ch < 0) {  // a leaf at level l + 1: its id and how many levels coarser it is
+                out = -1 - (((-1 - ch) << kRopeLevelBits) | (level - (l + 1)));
+                break;
+            }
+            if (l + 1 == level) {  // the node at the leaf's level: the neighbour is finer
+                out = ch;
                 break;
             }
             node = ch;
@@ -54,6 +58,7 @@ __global__ void ropes_kernel(const int32_t *__restrict__ child, const uint64_t *
 
 cudaError_t build_ropes(const TreeArrays &a, cudaStream_t s) {
     if (a.n_leaves == 0) return cudaSuccess;
+    if (a.n_leaves > kMaxRopeLeaves) return cudaErrorNotSupported;
     const int64_t n = 6 * a.n_leaves;
     ropes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.child, a.leaf_key, a.n_leaves, a.rope);
     return cudaGetLastError();

@@ -48,9 +48,10 @@ struct TreeArrays {
     void *palette = nullptr;
     uint32_t *leaf_rec = nullptr;
     int palette_bits = 0;
-    // ropes [L][6]: across face 2 axis + upper of a leaf, (node id at the leaf's level or leaf
-    // code -1 - v, its level), or (INT32_MIN, 0) outside the root; built by build_ropes
-    int2 *rope = nullptr;
+    // ropes [L][6]: across face 2 axis + upper of a leaf, the node id at the leaf's level (>= 0),
+    // or -1 - (v << kRopeLevelBits | levels coarser) for a leaf v, or INT32_MIN outside the root;
+    // built by build_ropes
+    int32_t *rope = nullptr;
 };
 
 inline void free_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStream_t s) {
@@ -83,7 +84,7 @@ inline cudaError_t alloc_tree_arrays(TreeArrays &a, const DevAlloc &al, cudaStre
     a.leaf_key = (uint64_t *)al.alloc((size_t)a.n_leaves * sizeof(uint64_t), s);
     a.sigma = al.alloc((size_t)a.n_leaves * sb, s);
     a.sh = al.alloc((size_t)a.n_leaves * (size_t)a.row_stride * sb, s);
-    a.rope = (int2 *)al.alloc((size_t)a.n_leaves * 6 * sizeof(int2), s);
+    a.rope = (int32_t *)al.alloc((size_t)a.n_leaves * 6 * sizeof(int32_t), s);
     if (!a.child || !a.node_parent || !a.node_key || !a.leaf_parent || !a.leaf_key || !a.sigma ||
         !a.sh || !a.rope) {
         free_tree_arrays(a, al, s);
