@@ -81,20 +81,25 @@ template <typename S, int K> struct Row {
     static constexpr int kVec = kBytes / 16;
 };
 
+// z[ch] = sum_k row[ch][k] Y_k in FP32, one 16-byte vector of the row at a time (each channel's
+// terms summed in k order)
 template <typename S, int K>
 __device__ __forceinline__ void leaf_z(const S *row, const float *Y, float z[3]) {
-    uint4 v[Row<S, K>::kVec];
+    constexpr int E = 16 / (int)sizeof(S);
     const uint4 *p = reinterpret_cast<const uint4 *>(row);
+    float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < Row<S, K>::kVec; i++) v[i] = __ldg(p + i);
-    const S *e = reinterpret_cast<const S *>(v);
+    for (int i = 0; i < Row<S, K>::kVec; i++) {
+        const uint4 v = __ldg(p + i);
+        const S *e = reinterpret_cast<const S *>(&v);
 #pragma unroll
-    for (int ch = 0; ch < 3; ch++) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < K; k++) acc = fmaf(Storage<S>::to_f32(e[ch * K + k]), Y[k], acc);
-        z[ch] = acc;
+        for (int j = 0; j < E; j++) {
+            const int idx = i * E + j;
+            if (idx < 3 * K) acc[idx / K] = fmaf(Storage<S>::to_f32(e[j]), Y[idx % K], acc[idx / K]);
+        }
     }
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) z[ch] = acc[ch];
 }
 
 // requests the 16-byte-aligned SH row into L1 ahead of its use (both ends: a row may straddle
