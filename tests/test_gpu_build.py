@@ -1,6 +1,7 @@
 """GPU octree build vs the oracle: structure bit-exact, seeded parameters bit-exact."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import seeded_inputs as si
@@ -63,5 +64,12 @@ def test_import_export_round_trip():
     for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key", "sigma", "sh"):
         np.testing.assert_array_equal(bits(ea[k]), bits(eb[k]), err_msg=k)
     assert ea["max_level"] == eb["max_level"]
+    # the imported tree (its face-neighbour table rebuilt on import) renders the same bits
+    o, d = si.random_rays(3000, 5)
+    rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+    ra, rb = torch.empty(3000, 3, device="cuda"), torch.empty(3000, 3, device="cuda")
+    dot.dot_render_forward(a, rays, dot.render_opts(), ra)
+    dot.dot_render_forward(b, rays, dot.render_opts(), rb)
+    assert torch.equal(ra, rb)
     a.free()
     b.free()

@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import seeded_inputs as si
-from helpers import oracle_side
+from helpers import assert_pixels_close, oracle_side
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +35,14 @@ def test_canonicalize_after_refines_matches_oracle():
         t, _, s64, h64, _ = oracle.refine(t, s64, h64, pm, sm, 8)
     L = tree.n_leaves
     assert np.any(np.diff(t["leaf_key"].astype(np.int64)) < 0)
+    # the refined tree (face-neighbour table rebuilt by each refine) renders as the oracle's
+    o, d = si.random_rays(4000, 19)
+    got = torch.empty(4000, 3, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()),
+                           dot.render_opts(background=(1, 1, 1), eps_T=1e-4), got)
+    lo, size = oracle.root_of(scene)
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, scene.sh_degree, o, d, eps_T=1e-4)
+    assert_pixels_close(got.cpu().numpy(), ref, scene.storage)
     cams = [si.pinhole((0.4, 1.1, 2.6), 640, 560, 700.0)]
     crays = dot.rays_cameras(dot.cameras_tensor(cams), 640, 560)
     o, d = si.random_rays(5000, 17)
