@@ -18,7 +18,7 @@ import ctypes
 import dataclasses
 import time
 from collections import deque
-from typing import List, Optional, Sequence
+from typing import List, Sequence
 
 import numpy as np
 

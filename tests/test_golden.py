@@ -1,7 +1,6 @@
 """Pins against values the paper prints (tests/golden/paper_values.txt, each line cited): the
 octree degree of Eq. 3, the grid and SH sizes and image sizes of the workloads, and the learning
 rates used as RMSProp defaults.  No GPU."""
-import math
 import os
 
 import numpy as np

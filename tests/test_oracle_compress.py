@@ -3,7 +3,6 @@ Sec. 4.1 to build the compressed models), no GPU: hand-worked splits, the longes
 rules, clustered data reconstructed exactly, nested refinement lowering the squared error, and the
 rendering of a compressed tree equal to the rendering of its expanded coefficients."""
 import numpy as np
-import pytest
 
 import oracle
 import seeded_inputs as si

@@ -1,7 +1,6 @@
 """Pins of the oracle's optimisation step (no GPU): the MSE loss of Algorithm 1 (optimization)
 and the RMSProp update of Sec. 3.3, fixed against closed forms, PyTorch's RMSprop in float64,
 finite differences, and the end-to-end chain MSE(render(params)) by finite differences."""
-import math
 
 import numpy as np
 import pytest
