@@ -19,7 +19,7 @@ calls.
 """
 from __future__ import annotations
 
-from typing import Optional
+from typing import Callable, Iterable, List, Optional, Tuple
 
 import torch
 
@@ -143,6 +143,34 @@ class Trainer:
         self.signal = torch.zeros(self.L, dtype=torch.float32, device="cuda")
         self._alloc_sparse_state()
         return {"passes": passes, "n_leaves": self.L, "n_nodes": self.tree.n_nodes}
+
+    # ---- Algorithm 1, the whole loop ----------------------------------------------------------
+    def fit(self, epoch_batches: Callable[[int], Iterable[Tuple[dot.dot_rays, torch.Tensor]]],
+            epochs: int, T: int, tau: float, gamma: float, depth_cap: int,
+            recursive: bool = True, prune_mode: int = dot.DOT_SELECT_THRESHOLD,
+            sample_mode: int = dot.DOT_SELECT_FRACTION, canonical: bool = False,
+            on_refine: Optional[Callable[[int, dict], None]] = None) -> List[float]:
+        """Algorithm 1: for epoch i = 1..epochs, one optimisation pass over
+        `epoch_batches(i)` -- the caller's (rays, target) batches in that epoch's permuted order --
+        accumulating the signal Q, then, when i is a multiple of T, pruning with tau (recursively
+        when asked) and sampling the top-gamma fraction.  `on_refine(i, plan)` is called after each
+        refine (the leaf numbering has changed: a caller holding per-leaf arrays remaps them with
+        self.leaf_map).  Returns the mean batch MSE of every epoch."""
+        losses = []
+        for i in range(1, epochs + 1):
+            self.loss_sum.zero_()
+            n = 0
+            for rays, target in epoch_batches(i):
+                self.step(rays, target)
+                n += 1
+            losses.append(float(self.loss_sum.item()) / max(n, 1))
+            if i % T == 0:
+                plan = self.refine(tau, gamma, depth_cap, recursive=recursive,
+                                   prune_mode=prune_mode, sample_mode=sample_mode,
+                                   canonical=canonical)
+                if on_refine is not None:
+                    on_refine(i, plan)
+        return losses
 
     def _marks(self, sel: dot.dot_select_opts):
         pm = torch.empty(self.L, dtype=torch.uint8, device="cuda")

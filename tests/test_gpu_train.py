@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import seeded_inputs as si
-from helpers import assert_sums_close, oracle_side
+from helpers import assert_pixels_close, assert_sums_close, oracle_side
 
 pytestmark = pytest.mark.gpu
 
@@ -210,3 +210,55 @@ def test_sparse_rmsprop_equals_dense(storage):
         d = np.abs(got - ref)
         assert (d <= lim).mean() > 0.999 and (d <= 3 * lim).all(), f"worst {(d / lim).max():.3g} x limit"
     tree.free()
+
+
+def test_fit_runs_algorithm_1():
+    """Trainer.fit: epochs of optimisation over the caller's batches with the signal accumulated,
+    pruning and sampling every T epochs (Algorithm 1).  Trained toward the renders of a tree of the
+    same structure with other seeded parameters, the epoch MSE falls; each refine reports its
+    plan and changes the leaves; every step's render stays in step with the oracle's render of
+    the trained parameters."""
+    import dataclasses
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.train import Trainer
+    scene = si.random_scene(73, max_depth=5, sh_degree=1, storage=si.STORAGE_F32, n_prims=3)
+    tree = dot.octree_from_scene(scene)
+    goal = dot.octree_from_scene(dataclasses.replace(scene, seed=scene.seed + 17))
+    opts = dot.render_opts(background=(1, 1, 1), eps_T=1e-4)
+    batches = []
+    for b in range(4):
+        o, d = si.random_rays(4096, 900 + b)
+        rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+        tgt = torch.empty(4096, 3, device="cuda")
+        dot.dot_render_forward(goal, rays, opts, tgt)
+        batches.append((rays, tgt))
+    rng = np.random.default_rng(4)
+
+    def epoch(i):  # the epoch's batches in a permuted order
+        return [batches[j] for j in rng.permutation(len(batches))]
+
+    tr = Trainer(tree, opts, dot.dot.rmsprop_opts(0.1, 0.01, 0.9, 1e-8),
+                 signal_mode=dot.dot.DOT_SIGNAL_MAX_WEIGHT)
+    refines = []
+    L0 = tree.n_leaves
+    losses = tr.fit(epoch, epochs=6, T=3, tau=1e-3, gamma=0.02, depth_cap=6,
+                    on_refine=lambda i, plan: refines.append((i, plan)))
+    torch.cuda.synchronize()
+    assert tree.status() == 0
+    assert [i for i, _ in refines] == [3, 6]
+    assert all(p["passes"] for _, p in refines) and tree.n_leaves != L0
+    assert losses[2] < losses[1] < losses[0] and losses[-1] < losses[0], losses
+    # the trained tree renders as the oracle's render of its exported parameters
+    ex = tree.export()
+    t = {k: ex[k] for k in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key")}
+    lo, size = oracle.root_of(scene)
+    o, d = si.random_rays(3000, 77)
+    got = torch.empty(3000, 3, device="cuda")
+    dot.dot_render_forward(tree, dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()),
+                           opts, got)
+    s64 = ex["sigma"].astype(np.float64)
+    h64 = ex["sh"].astype(np.float64)
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, 1, o, d, eps_T=1e-4)
+    assert_pixels_close(got.cpu().numpy(), ref, scene.storage)
+    tree.free()
+    goal.free()
