@@ -273,3 +273,35 @@ def test_views_to_host_argument_errors():
     # no views: nothing to do
     dot.dot.dot_render_views_host(tree, recs[:0], 64, 48, opts, torch.zeros(0))
     tree.free()
+
+
+@pytest.mark.parametrize("depth,radius,storage", [(12, 0.01, si.STORAGE_F32), (12, 0.01, si.STORAGE_F16),
+                                                  (16, 0.0006, si.STORAGE_F32)])
+def test_deep_tree_matches_oracle(depth, radius, storage):
+    """Trees down to the finest level (16): a small sphere and box carved deep, so that rays near
+    them cross neighbours up to 15 levels apart; rays aimed at the primitives."""
+    import paper_2307_15333_gb300 as dot
+    c = np.array([0.1, -0.05, 0.02])
+    prims = si._prims([si.sphere(tuple(c), radius, (0.0, 0.0, 0.0), 1.0),
+                       si.box(tuple(c - [2 * radius, radius, 0.5 * radius]),
+                              tuple(c + [-0.5 * radius, 2 * radius, 2 * radius]), (0.0, 0.0, 0.0), 1.0)])
+    scene = si.Scene(f"deep{depth}", (0.0, 0.0, 0.0), 1.0, depth, 1, storage, prims,
+                     5.0 / radius, 50.0 / radius, 0.4, 0.2, 41)
+    tree = dot.octree_from_scene(scene)
+    assert tree.info().max_level == depth
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    rng = np.random.default_rng(depth)
+    u = rng.normal(size=(3000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    o = (c + 3.0 * u).astype(np.float32)
+    aim = c + rng.uniform(-3 * radius, 3 * radius, size=(3000, 3))
+    d = aim - o.astype(np.float64)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    got, Tg = _gpu_render(tree, o, d)
+    ref, Tr, _ = oracle.render(t, lo, size, s64, h64, 1, o, d)
+    assert_pixels_close(got, ref, storage)
+    assert_pixels_close(Tg, Tr, storage, what="T")
+    assert np.mean(Tr < 0.5) > 0.2                     # many rays do hit the primitives
+    assert tree.status() == 0
+    tree.free()
