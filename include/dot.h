@@ -141,6 +141,10 @@ typedef struct {
     int32_t pad2_;
     void *palette;         /* device [2^palette_bits][sh_row_stride], storage type, or NULL */
     uint32_t *leaf_record; /* device [n_leaves]: density bits | palette row << 16, or NULL */
+    int32_t *rope;         /* device [n_leaves][6], read-only: across face 2 axis + (1 for the upper
+                              face) of leaf v, the node id (>= 0) at v's level when the tree is
+                              finer there, else -1 - (u << 4 | d) for the leaf u covering that
+                              place, d levels coarser than v, or INT32_MIN outside the root */
 } dot_tree_info;
 
 /* Host copy of a tree (checkpoint / import).  sh is [n_leaves][3K] without row padding. */

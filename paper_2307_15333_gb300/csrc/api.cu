@@ -297,6 +297,7 @@ int dot_tree_get_info(const dot_tree *t, dot_tree_info *info) {
     info->palette_bits = t->a.palette_bits;
     info->palette = t->a.palette;
     info->leaf_record = t->a.leaf_rec;
+    info->rope = t->a.rope;
     return DOT_OK;
 }
 

@@ -89,7 +89,7 @@ class dot_tree_info(ctypes.Structure):
                 ("center", ctypes.c_float * 3), ("half_size", ctypes.c_float),
                 ("child", P), ("node_parent", P), ("node_key", P), ("leaf_parent", P),
                 ("leaf_key", P), ("sigma", P), ("sh", P), ("palette_bits", ctypes.c_int32),
-                ("pad2_", ctypes.c_int32), ("palette", P), ("leaf_record", P)]
+                ("pad2_", ctypes.c_int32), ("palette", P), ("leaf_record", P), ("rope", P)]
 
 
 class dot_host_tree(ctypes.Structure):
@@ -311,6 +311,12 @@ class Octree:
     def sigma(self) -> torch.Tensor:
         inf = self.info()
         return _view(inf.sigma, (inf.n_leaves,), _TORCH_OF_STORAGE[inf.storage], self)
+
+    @property
+    def rope(self) -> torch.Tensor:
+        """[L, 6] int32 view of the face-neighbour table (read-only; see dot_tree_info)."""
+        inf = self.info()
+        return _view(inf.rope, (inf.n_leaves, 6), torch.int32, self)
 
     @property
     def palette_bits(self) -> int:
