@@ -150,3 +150,38 @@ def test_slot_tables_serve_compressed_trees():
         dot.dot.dot_render_slots([trees[0], plain], table, 4, opts, counter)
     for t in trees + [plain]:
         t.free()
+
+
+def test_full_size_compressed_model_matches_oracle():
+    """The bench's compressed model at full size: 2.9 M-leaf tree, 2^16-row palette.  Palette
+    indices bit-exact against the oracle's median cut; sampled pixels of view-ordered 800x800
+    camera renders (the bench's launch configuration) against the oracle's render of the
+    palette rows."""
+    import paper_2307_15333_gb300 as dot
+    scene, cams = si.config_nerf_synthetic(n_views=100)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    L, K = s64.size, scene.n_coeffs
+    idx_ref, pal_ref = oracle.median_cut(h64.reshape(L, 3 * K), 16)
+    dot.dot.dot_compress_sh(tree, 16)
+    idx = tree.palette_index.cpu().numpy()
+    np.testing.assert_array_equal(idx, idx_ref)
+    pal = tree.palette.float().cpu().numpy().astype(np.float64).reshape(1 << 16, 3 * K)
+    assert (np.abs(pal - pal_ref) <= _spacing(pal_ref, scene.storage)).all()
+    cam_t = dot.cameras_tensor(cams)
+    order = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
+    rgb = torch.empty(100 * 800 * 800, 3, device="cuda")
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    dot.dot_render_forward(tree, dot.rays_cameras(cam_t, 800, 800, order), opts, rgb)
+    torch.cuda.synchronize()
+    assert tree.status() == 0
+    lo, size = oracle.root_of(scene)
+    rows = pal[idx].reshape(L, 3, K)
+    rng = np.random.default_rng(6)
+    for v in (0, 61):
+        pix = rng.integers(0, 800 * 800, 1500)
+        o, d = si.camera_rays(cams[v], pix)
+        ref, _, _ = oracle.render(t, lo, size, s64, rows, 3, o, d)
+        got = rgb[v * 800 * 800 + torch.from_numpy(pix).cuda()].cpu().numpy()
+        assert np.abs(got - ref).max() <= ABS16
+    tree.free()
