@@ -26,6 +26,12 @@ constexpr int kTrainThreads = 256;
 #ifndef DOT_SPARSE_MINB
 #define DOT_SPARSE_MINB 4
 #endif
+// 1: the optimiser state rows stream through L2 with evict-first loads and stores, so that the
+// tree's nodes, ropes and densities stay in L2 for the next step's march (258.6 -> 252.2 us per
+// training step)
+#ifndef DOT_SPARSE_STREAM
+#define DOT_SPARSE_STREAM 1
+#endif
 
 // grad[r][c] = 2 (rgb - target) / (3 R); loss_sum += sum (rgb - target)^2 / (3 R)
 __global__ void __launch_bounds__(kTrainThreads)
@@ -366,8 +372,13 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     if (ok[u]) {
+#if DOT_SPARSE_STREAM
+                        g[u] = __ldcs(reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width) + q);
+                        m[u] = __ldcs(reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width) + q);
+#else
                         g[u] = reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width)[q];
                         m[u] = reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width)[q];
+#endif
                         pv[u] = *reinterpret_cast<const typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q);
                     }
                 }
@@ -385,10 +396,19 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
                     p[1] = rms_update(p[1], g[u].y, mm.y, o);
                     p[2] = rms_update(p[2], g[u].z, mm.z, o);
                     p[3] = rms_update(p[3], g[u].w, mm.w, o);
+#if DOT_SPARSE_STREAM
+                    __stcs(reinterpret_cast<float4 *>(ms_sh + (int64_t)v[u] * width) + q, mm);
+#else
                     reinterpret_cast<float4 *>(ms_sh + (int64_t)v[u] * width)[q] = mm;
+#endif
                     *reinterpret_cast<typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q) = V::make(p);
                     if (o.zero_grad)
+#if DOT_SPARSE_STREAM
+                        __stcs(reinterpret_cast<float4 *>(grad_sh + (int64_t)v[u] * width) + q,
+                               make_float4(0.f, 0.f, 0.f, 0.f));
+#else
                         reinterpret_cast<float4 *>(grad_sh + (int64_t)v[u] * width)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
                 }
             }
         } else {
