@@ -689,8 +689,8 @@ def run_dot(args):
     e2e = {"value": R * e2e_steps * ws / e2e_s / 1e6, "unit": "Mrays/s",
            "h2d_bytes_per_step": int(cams_host.numel() * 4),
            "d2h_bytes_per_step": int(out_host.numel() * 4),
-           "call": "dot_render_views_host (host cameras in, host images out; chunks of about "
-                   "2^23 rays, each chunk's copy overlapping the next chunks' march)"}
+           "call": "dot_render_views_host (host cameras in, pinned host images out, written in "
+                   "place by the render launch)"}
     del ws_views
 
     # ---- refine pass (signal, selection, prune / sample), once, on the resident tree ----

@@ -297,13 +297,15 @@ int dot_render_forward(const dot_tree *tree, const dot_rays *rays, const dot_ren
 /*
  * dot_render_views_host -- dot_render_forward over n_cameras whole camera views whose cameras and
  * images live in HOST memory (Eq. 1-2 per pixel; every value equals dot_render_forward's for the
- * same camera).  The views are rendered in chunks of about 2^23 rays (the views left after the
- * full chunks in halving chunks down to one view), in view_order when given so that consecutive
- * views reuse the leaves left in L2, alternately on `stream` and on a second render stream, into
- * a ring of three chunk buffers in the workspace; each finished chunk is copied to the host on a
- * copy stream while the next chunks render, so the device-to-host copy overlaps the march.  The
- * work is ordered after what `stream` already holds; the call returns after every image is in
- * rgb (and T_final).
+ * same camera).  The views are rendered in view_order when given, so that consecutive views
+ * reuse the leaves left in L2.  When rgb (and T_final) lie in page-locked host memory mapped into
+ * the device's address space (cudaHostAlloc, or cudaHostRegister with mapping; with unified
+ * addressing every page-locked allocation is), one launch writes every image in place.
+ * Otherwise the views are rendered in chunks of about 2^23 rays (the views left after the full
+ * chunks in halving chunks down to one view), alternately on `stream` and on a second render
+ * stream, into a ring of three chunk buffers in the workspace, and each finished chunk is copied
+ * to the host on a copy stream while the next chunks render.  The work is ordered after what
+ * `stream` already holds; the call returns after every image is in rgb (and T_final).
  * cameras: host [n_cameras] dot_camera (copied to the workspace by this call).  width, height: the
  * resolution shared by every camera.  view_order: host [n_cameras] or NULL -- the render order, a
  * permutation of 0..n_cameras-1 (anything else fails with DOT_ERR_INVALID_ARG before any work).

@@ -861,6 +861,12 @@ extern "C" int dot_camera_order(const dot_camera *cams, int32_t n, int32_t *orde
 // whole views to host memory: chunked march on the caller's stream (and a second render stream),
 // device-to-host copies of the finished chunks on a copy stream
 // ---------------------------------------------------------------------------------------------
+// 1: page-locked, mapped host images are written in place by one launch (no copies): 100 views of
+// 800x800 to host memory in 8.66 ms against 9.07 ms through the chunked copies (8.65 ms on the
+// device alone)
+#ifndef DOT_VIEWS_DIRECT
+#define DOT_VIEWS_DIRECT 1
+#endif
 // log2 of the rays per chunk, about
 #ifndef DOT_VIEWS_CHUNK_LOG2
 #define DOT_VIEWS_CHUNK_LOG2 23
@@ -891,7 +897,7 @@ struct ViewsPlan {
     int32_t chunk_views = 0;  // views of a full chunk (the capacity of a ring buffer)
     int32_t slots = 0;
     std::vector<int32_t> first;  // the chunks: first view (in render order) of each, then n
-    int64_t cams_bytes = 0, rgb_bytes = 0, T_bytes = 0, total = 0;
+    int64_t cams_bytes = 0, order_bytes = 0, rgb_bytes = 0, T_bytes = 0, total = 0;
 };
 
 int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
@@ -916,9 +922,10 @@ bool plan_views(int32_t n, int32_t W, int32_t H, bool with_T, ViewsPlan &p) {
     p.first.push_back(n);
     p.slots = std::min<int32_t>(kViewSlots, (int32_t)p.first.size() - 1);
     p.cams_bytes = align256((int64_t)n * (int64_t)sizeof(dot_camera));
+    p.order_bytes = align256((int64_t)n * (int64_t)sizeof(int32_t));
     p.rgb_bytes = align256(p.chunk_views * p.per_view * 3 * (int64_t)sizeof(float));
     p.T_bytes = with_T ? align256(p.chunk_views * p.per_view * (int64_t)sizeof(float)) : 0;
-    p.total = p.cams_bytes + p.slots * (p.rgb_bytes + p.T_bytes);
+    p.total = p.cams_bytes + p.order_bytes + p.slots * (p.rgb_bytes + p.T_bytes);
     return true;
 }
 
@@ -945,6 +952,24 @@ struct ViewsPipe {
         }
     }
 };
+
+// The device address of host buffer [p, p + bytes) when all of it lies in one page-locked
+// allocation mapped into the device's address space, else null (pageable or foreign memory).
+float *mapped_device_ptr(float *p, size_t bytes) {
+    cudaPointerAttributes a0{}, a1{};
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, reinterpret_cast<char *>(p) + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer ||
+        !a1.devicePointer)
+        return nullptr;
+    if (static_cast<char *>(a1.devicePointer) - static_cast<char *>(a0.devicePointer) !=
+        static_cast<ptrdiff_t>(bytes - 1))
+        return nullptr;
+    return static_cast<float *>(a0.devicePointer);
+}
 
 // device-to-host copies of `cnt` views of one chunk: view j of the chunk goes to host view
 // order[j]; runs of consecutive views go in one copy
@@ -1004,14 +1029,45 @@ extern "C" int dot_render_views_host(const dot_tree *t, const dot_camera *camera
     } else {
         for (int32_t i = 0; i < n; i++) order[(size_t)i] = i;
     }
-    std::vector<dot_camera> cams((size_t)n);  // in render order; alive until the call returns
-    for (int32_t i = 0; i < n; i++) cams[(size_t)i] = cameras[order[(size_t)i]];
-
     char *ws = static_cast<char *>(workspace);
     dot_camera *d_cams = reinterpret_cast<dot_camera *>(ws);
+    const dot::TreeView tv = view_of(t);
+    const char *where = "dot_render_views_host";
+
+    // page-locked, mapped host images: one launch writes every view in place, no copies
+    float *rgb_dev = DOT_VIEWS_DIRECT ? mapped_device_ptr(rgb, (size_t)(n * p.per_view * 3) * sizeof(float)) : nullptr;
+    float *T_dev = (rgb_dev && T_final) ? mapped_device_ptr(T_final, (size_t)(n * p.per_view) * sizeof(float)) : nullptr;
+    if (rgb_dev && (!T_final || T_dev)) {
+        int32_t *d_order = reinterpret_cast<int32_t *>(ws + p.cams_bytes);
+        std::vector<dot_camera> cams_in(cameras, cameras + n);  // alive until the call returns
+        cudaStream_t s = S(stream);
+        API_CK(cudaMemcpyAsync(d_cams, cams_in.data(), (size_t)n * sizeof(dot_camera),
+                               cudaMemcpyHostToDevice, s), where);
+        API_CK(cudaMemcpyAsync(d_order, order.data(), (size_t)n * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s), where);
+        dot_rays r{};
+        r.kind = DOT_RAYS_CAMERAS;
+        r.n_cameras = n;
+        r.cameras = d_cams;
+        r.width = width;
+        r.height = height;
+        r.view_order = d_order;
+        dot::RaySource rs;
+        int64_t R = 0;
+        if ((rc = make_rays(&r, rs, R))) return rc;
+        dot::RenderIO io{};
+        io.rgb = rgb_dev;
+        io.T_final = T_dev;
+        io.status = t->status;
+        API_CK(dot::launch_march_fwd(t->a.storage, t->a.sh_degree, exact, tv, rs, rp, io, s), where);
+        API_CK(cudaStreamSynchronize(s), where);
+        return DOT_OK;
+    }
+
+    std::vector<dot_camera> cams((size_t)n);  // in render order; alive until the call returns
+    for (int32_t i = 0; i < n; i++) cams[(size_t)i] = cameras[order[(size_t)i]];
     ViewsPipe pipe;
     pipe.render[0] = pipe.render[1] = S(stream);
-    const char *where = "dot_render_views_host";
     API_CK(cudaStreamCreateWithFlags(&pipe.copy, cudaStreamNonBlocking), where);
     API_CK(cudaEventCreateWithFlags(&pipe.ready, cudaEventDisableTiming), where);
     for (int i = 0; i < p.slots; i++) {
@@ -1027,14 +1083,14 @@ extern "C" int dot_render_views_host(const dot_tree *t, const dot_camera *camera
         API_CK(cudaEventRecord(pipe.ready, pipe.render[0]), where);  // the cameras have arrived
         API_CK(cudaStreamWaitEvent(pipe.render[1], pipe.ready, 0), where);
     }
-    const dot::TreeView tv = view_of(t);
     const int32_t n_chunks = (int32_t)p.first.size() - 1;
     for (int32_t k = 0; k < n_chunks; k++) {
         const int slot = k % p.slots;
         cudaStream_t rs_k = pipe.render[k & 1];
         const int32_t first = p.first[(size_t)k];
         const int32_t cnt = p.first[(size_t)k + 1] - first;
-        float *d_rgb = reinterpret_cast<float *>(ws + p.cams_bytes + slot * (p.rgb_bytes + p.T_bytes));
+        float *d_rgb = reinterpret_cast<float *>(ws + p.cams_bytes + p.order_bytes +
+                                                 slot * (p.rgb_bytes + p.T_bytes));
         float *d_T = T_final ? reinterpret_cast<float *>(reinterpret_cast<char *>(d_rgb) + p.rgb_bytes) : nullptr;
         if (k >= p.slots)  // the slot's previous chunk has left for the host
             API_CK(cudaStreamWaitEvent(rs_k, pipe.copied[slot], 0), where);

@@ -67,21 +67,22 @@ def test_import_rejects_malformed_trees_on_host():
 
 
 def test_render_views_host_workspace_sizes():
-    """Workspace of dot_render_views_host: the cameras (72 B each), then up to three chunk buffers
-    of a full chunk (about 2^23 rays) each, every part rounded up to 256 bytes; worked by hand."""
+    """Workspace of dot_render_views_host: the cameras (72 B each), the view order (4 B each), then
+    up to three chunk buffers of a full chunk (about 2^23 rays) each, every part rounded up to
+    256 bytes; worked by hand."""
     from paper_2307_15333_gb300 import dot
     f = dot.dot_render_views_host_workspace
     # 100 views of 800x800 (64 M rays): chunks of 13 views (7 full, then 5, 2, 1, 1), three buffers
     # of 13 x 640000 x 12 B
-    assert f(100, 800, 800) == 7424 + 3 * 99840000
-    assert f(100, 800, 800, True) == 7424 + 3 * (99840000 + 33280000)
+    assert f(100, 800, 800) == 7424 + 512 + 3 * 99840000
+    assert f(100, 800, 800, True) == 7424 + 512 + 3 * (99840000 + 33280000)
     # 7 views of 320x240 (537600 rays): one chunk, one buffer
-    assert f(7, 320, 240) == 512 + 6451200
-    assert f(7, 320, 240, True) == 512 + 6451200 + 2150400
+    assert f(7, 320, 240) == 512 + 256 + 6451200
+    assert f(7, 320, 240, True) == 512 + 256 + 6451200 + 2150400
     # one 8x8 view: 768 B of colour
-    assert f(1, 8, 8) == 256 + 768
+    assert f(1, 8, 8) == 256 + 256 + 768
     # two 4096x4096 views (2 x 2^24 rays): one view per chunk, two buffers
-    assert f(2, 4096, 4096) == 256 + 2 * 201326592
+    assert f(2, 4096, 4096) == 256 + 256 + 2 * 201326592
     assert f(0, 800, 800) == 0
     for bad in ((-1, 8, 8), (65536, 8, 8), (1, 0, 8), (1, 8, 65537)):
         assert f(*bad, 0) == -1

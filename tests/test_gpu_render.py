@@ -213,11 +213,12 @@ def _forward_all(dot, tree, cam_t, W, H, opts):
 
 
 def test_views_to_host_match_the_device_forward():
-    """dot_render_views_host (chunks of about 2^23 rays over two render streams, three chunk
-    buffers in a ring, copies on a third stream) writes the same bits as one dot_render_forward
-    launch: 40 views of 800x800 go in seven chunks (10, 10, 10, 5, 3, 1, 1 views), so the ring
-    wraps; with and without a view order and T, into pinned and pageable host buffers; a given
-    workspace is reused."""
+    """dot_render_views_host writes the same bits as one dot_render_forward launch, both ways:
+    into pinned (mapped) host buffers by one launch writing in place, and into pageable ones
+    through chunks of about 2^23 rays over two render streams, three chunk buffers in a ring and
+    copies on a third stream (40 views of 800x800 go in seven chunks: 10, 10, 10, 5, 3, 1, 1
+    views, so the ring wraps); with and without a view order and T; a given workspace is
+    reused."""
     import paper_2307_15333_gb300 as dot
     scene = si.random_scene(21, max_depth=6, sh_degree=3, storage=si.STORAGE_F16, n_prims=5)
     tree = dot.octree_from_scene(scene)
