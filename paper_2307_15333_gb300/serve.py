@@ -14,8 +14,10 @@ Host bookkeeping (pool, packing, trace) is plain Python and runs without a GPU; 
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import dataclasses
+import gc
 import time
 from collections import deque
 from typing import List, Sequence
@@ -123,6 +125,19 @@ def percentiles(reqs: Sequence[Request]):
 # ----------------------------------------------------------------------------------------------
 # device side
 # ----------------------------------------------------------------------------------------------
+@contextlib.contextmanager
+def _no_gc_pauses():
+    """The serving loops run with Python's cyclic garbage collector paused (a full collection of
+    a large process can stall the host loop for tens of milliseconds); restored afterwards."""
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
 class _Table:
     def __init__(self, torch, max_slots):
         nbytes = HEADER_BYTES + SLOT_BYTES * max_slots
@@ -182,6 +197,10 @@ class BatchedServer:
 
     def run(self, trace: Sequence[Request], clock=time.perf_counter):
         """Replays the trace in real time; fills r.done for every request."""
+        with _no_gc_pauses():
+            return self._run(trace, clock)
+
+    def _run(self, trace: Sequence[Request], clock):
         pending: deque = deque()
         free_tables = list(self.tables)
         busy: List[_Table] = []
@@ -253,6 +272,11 @@ class PlainServer:
         self.cams = torch.zeros(18, dtype=torch.float32, pin_memory=True)
 
     def run(self, trace: Sequence[Request], clock=time.perf_counter):
+        """Replays the trace in real time; fills r.done for every request."""
+        with _no_gc_pauses():
+            return self._run(trace, clock)
+
+    def _run(self, trace: Sequence[Request], clock):
         torch, dot = self.torch, self.dot
         pending: deque = deque()
         inflight: deque = deque()
