@@ -764,8 +764,9 @@ def run_dot(args):
             "config": {"workload": WORKLOAD, "leaves": L, "nodes": tree.n_nodes,
                        "views": len(cams), "width": W, "height": H, "rays_per_step": R,
                        "sh_degree": scene.sh_degree, "leaf_storage": "f16",
-                       "l2": "inputs larger than L2, no flush: leaves %.0f MB + nodes %.0f MB "
-                             "vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6),
+                       "l2": "inputs larger than L2, no flush: leaves %.0f MB + nodes %.0f MB + "
+                             "ropes %.0f MB vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6,
+                                                            L * 24 / 1e6),
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "train": train_res,
