@@ -545,6 +545,7 @@ def run_dot(args):
     W, H = cams[0].width, cams[0].height
     tree = dot.octree_from_scene(scene)
     L = tree.n_leaves
+    N_nodes = tree.n_nodes                                # the headline tree (refined later)
     cam_t = dot.cameras_tensor(cams)
     # views rendered in a nearest-neighbour chain so that consecutive views reuse L2
     order_t = torch.from_numpy(dot.dot.dot_camera_order(cam_t.cpu().numpy())).cuda()
@@ -744,7 +745,7 @@ def run_dot(args):
                 "segments_per_ray": seg / R, "occupied_per_ray": occ / R,
                 "occupied_leaves_touched": u_leaf}
     # compulsory bytes: what one launch must move at least once from HBM
-    compulsory = u_leaf * P + tree.n_nodes * 32 + n_empty * bs + R * 12
+    compulsory = u_leaf * P + N_nodes * 32 + n_empty * bs + R * 12
     roofline["compulsory"] = {
         "bytes": compulsory,
         "what": "distinct occupied leaves x payload + every node row + every empty density "
@@ -761,11 +762,11 @@ def run_dot(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "leaves": L, "nodes": tree.n_nodes,
+            "config": {"workload": WORKLOAD, "leaves": L, "nodes": N_nodes,
                        "views": len(cams), "width": W, "height": H, "rays_per_step": R,
                        "sh_degree": scene.sh_degree, "leaf_storage": "f16",
                        "l2": "inputs larger than L2, no flush: leaves %.0f MB + nodes %.0f MB + "
-                             "ropes %.0f MB vs 129 MB L2" % (L * P / 1e6, tree.n_nodes * 32 / 1e6,
+                             "ropes %.0f MB vs 129 MB L2" % (L * P / 1e6, N_nodes * 32 / 1e6,
                                                             L * 24 / 1e6),
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
