@@ -233,10 +233,12 @@ def test_views_to_host_match_the_device_forward():
     order = dot.dot.dot_camera_order(recs.numpy())
     ws = torch.empty(dot.dot.dot_render_views_host_workspace(n, W, H, True), dtype=torch.uint8,
                      device="cuda")
-    for pinned, view_order, with_T in ((True, order, True), (False, None, False),
-                                       (True, None, True), (False, order, False)):
+    # (pinned images, view order, T wanted, pinned T): a pageable T sends both through the copies
+    for pinned, view_order, with_T, pinned_T in ((True, order, True, True), (False, None, False, False),
+                                                 (True, None, True, True), (False, order, False, False),
+                                                 (True, order, True, False)):
         out = torch.full((n, H, W, 3), -1.0, pin_memory=pinned)
-        T = torch.full((n, H, W), -1.0, pin_memory=pinned) if with_T else None
+        T = torch.full((n, H, W), -1.0, pin_memory=pinned_T) if with_T else None
         dot.dot.dot_render_views_host(tree, recs, W, H, opts, out, T_host=T,
                                       view_order=view_order, workspace=ws)
         assert torch.equal(out, ref)
