@@ -341,7 +341,8 @@ int dot_render_slots(dot_tree *const *trees, int32_t n_trees, const void *table,
 
 /*
  * dot_render_backward -- gradient of L = sum_r grad_rgb[r] . rgb[r] with respect to the leaf
- * parameters, by recomputing each ray's march (no per-sample state from the forward):
+ * parameters (the differentiable render of Sec. 3 Preliminaries, Eq. 1-2), by recomputing each
+ * ray's march (no per-sample state from the forward):
  *   dL/dsh[v][ch][k] += g_ch w_i act'(z_ch) Y_k,
  *   dL/dsigma[v]     += [sigma_v > 0] delta_i sum_ch g_ch (T_{i+1} c_ch - (C_ch - C_{<=i,ch})).
  * grad_rgb, rgb: device [R][3] (rgb = this tree's forward output for the same rays and opts);
@@ -388,8 +389,9 @@ int dot_select_masks(const dot_tree *tree, const float *signal, const dot_select
                      uint8_t *prune_mark, uint8_t *sample_mark, void *stream);
 
 /*
- * dot_select_masks_noalloc -- the same prune and sample marks as dot_select_masks, computed
- * without allocating any device memory.  The paper has no counterpart to this call.
+ * dot_select_masks_noalloc -- the same prune and sample marks as dot_select_masks (Sec. 3.2,
+ * Algorithm 1), computed without allocating any device memory.  The paper has no counterpart to
+ * this call.
  *
  * It exists for applications that cannot have the library allocate while it works: a process
  * that reserves its whole device-memory budget at start-up (an engine or renderer that owns the
@@ -415,7 +417,8 @@ int dot_select_masks_noalloc(const dot_tree *tree, const float *signal,
                              uint8_t *sample_mark, void *stream);
 
 /*
- * dot_refine_plan -- the sizes dot_refine_prune will produce for these marks (synchronises).
+ * dot_refine_plan -- the sizes dot_refine_prune will produce for these marks (the merges of Eq. 3
+ * and the subdivisions of Eq. 4; synchronises).
  */
 int dot_refine_plan(const dot_tree *tree, const uint8_t *prune_mark, const uint8_t *sample_mark,
                     int32_t depth_cap, dot_refine_counts *out, void *stream);
@@ -471,9 +474,9 @@ int dot_rmsprop_step(dot_tree *tree, float *grad_sigma, float *grad_sh, float *m
                      float *ms_sh, const dot_rmsprop_opts *opts, void *stream);
 
 /*
- * dot_rmsprop_step_sparse -- dot_rmsprop_step restricted to the leaves whose `touched` flag is set
- * (dot_render_backward sets it for every leaf it gives a gradient), with the same results up to
- * FP32 rounding.  A leaf nobody touched has zero gradients, so the dense update would only
+ * dot_rmsprop_step_sparse -- dot_rmsprop_step (RMSProp, Sec. 3.3) restricted to the leaves whose
+ * `touched` flag is set (dot_render_backward sets it for every leaf it gives a gradient), with
+ * the same results up to FP32 rounding.  A leaf nobody touched has zero gradients, so the dense update would only
  * multiply its mean squares by rho; that decay is deferred and applied as rho^k for the k steps
  * it sat out, the next time the leaf is touched or by dot_rmsprop_flush.
  * touched: device [L] uint8, read and cleared; last_step: device [L] int32, the step up to which
@@ -487,7 +490,7 @@ int dot_rmsprop_step_sparse(dot_tree *tree, float *grad_sigma, float *grad_sh, f
                             int32_t *work, const dot_rmsprop_opts *opts, void *stream);
 
 /*
- * dot_rmsprop_flush -- applies every deferred decay up to step `step`:
+ * dot_rmsprop_flush -- applies every deferred RMSProp decay (Sec. 3.3) up to step `step`:
  * ms <- rho^(step - last_step) ms and last_step <- step for every leaf (before reading the mean
  * squares, refining the tree or switching to dot_rmsprop_step).
  */
