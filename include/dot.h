@@ -73,6 +73,9 @@ extern "C" {
 #define DOT_SELECT_THRESHOLD 1 /* prune: S <= value; sample: S > value (Sec. 3.2) */
 #define DOT_SELECT_FRACTION 2  /* prune: ceil(value L) smallest by (S asc, id asc);
                                   sample: ceil(value L) largest by (S desc, id asc) (Algorithm 1) */
+#define DOT_SELECT_QUANTILE 3  /* the FRACTION selection widened to every leaf whose signal equals
+                                  the last one taken: prune S <= the ceil(value L)-th smallest, sample
+                                  S >= the ceil(value L)-th largest (a threshold at a quantile) */
 
 #define DOT_MERGE_MEAN 0
 #define DOT_MERGE_SUM 1
@@ -382,16 +385,17 @@ int dot_accumulate_signal(const dot_tree *tree, const dot_rays *rays, const dot_
 
 /*
  * dot_select_masks -- prune and sample marks from the signal (Sec. 3.2; Algorithm 1 pruning
- * and sampling).  Rank selections break ties by leaf id.  signal: device [L] float;
+ * and sampling).  Rank selections break ties by leaf id.  Signals compare as floats: -0 equals
+ * +0, and a NaN is never marked by a threshold and comes after every number in both rank orders
+ * (taken only when k exceeds the count of numbers).  signal: device [L] float;
  * prune_mark, sample_mark: device [L] uint8 (written 0/1).
  */
 int dot_select_masks(const dot_tree *tree, const float *signal, const dot_select_opts *opts,
                      uint8_t *prune_mark, uint8_t *sample_mark, void *stream);
 
 /*
- * dot_select_masks_noalloc -- the same prune and sample marks as dot_select_masks (Sec. 3.2,
- * Algorithm 1), computed without allocating any device memory.  The paper has no counterpart to
- * this call.
+ * dot_select_masks_noalloc -- the same prune and sample marks as dot_select_masks, computed
+ * without allocating any device memory.  The paper has no counterpart to this call.
  *
  * It exists for applications that cannot have the library allocate while it works: a process
  * that reserves its whole device-memory budget at start-up (an engine or renderer that owns the
@@ -405,8 +409,10 @@ int dot_select_masks(const dot_tree *tree, const float *signal, const dot_select
  * radix-select histogram and state, and one count per tile of 4096 leaves), which every GPU
  * that loads the library keeps until the process exits.  Limits and behaviour:
  *  - trees of at most 2^26 (67,108,864) leaves; larger trees return DOT_ERR_INVALID_ARG;
- *  - the first call on each device looks up the array's device address (with that device
- *    current); make that first call before any stream capture;
+ *  - a call made outside stream capture looks up the array's device address with the calling
+ *    device current; a call made while its stream is being captured reuses the address the last
+ *    call on that device found (DOT_ERR_CUDA if there was none), so make one call on each device
+ *    before any stream capture;
  *  - every call on a device shares the array and leaves its last contents there (the call clears
  *    what must start at zero itself); calls whose work overlaps on the GPU, for example on two
  *    streams without ordering, race on it and can return wrong marks, so order such calls.

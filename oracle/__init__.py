@@ -32,6 +32,7 @@ SIGNAL_MAX_WEIGHT = 2
 SELECT_NONE = 0
 SELECT_THRESHOLD = 1
 SELECT_FRACTION = 2
+SELECT_QUANTILE = 3
 
 
 def build(force: bool = False) -> str:

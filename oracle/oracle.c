@@ -429,22 +429,31 @@ int oracle_backward(const otree *t, const oopts *op, const double *sigma, const 
 /* ------------------------------------------------------------------------------------------ */
 
 static const float *g_sort_sig;
+/* Selection order of two signals: numeric order, with -0 and +0 equal (IEEE comparison) and a
+ * NaN after every number in either direction; equal keys fall back to the leaf id. */
+static int sig_order(float x, float y, int desc) {
+    int nx = isnan(x), ny = isnan(y);
+    if (nx || ny) return nx - ny;
+    if (x < y) return desc ? 1 : -1;
+    if (x > y) return desc ? -1 : 1;
+    return 0;
+}
 static int cmp_desc(const void *a, const void *b) {
     int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
-    float x = g_sort_sig[i], y = g_sort_sig[j];
-    if (x > y) return -1;
-    if (x < y) return 1;
+    int c = sig_order(g_sort_sig[i], g_sort_sig[j], 1);
+    if (c) return c;
     return (i > j) - (i < j);
 }
 static int cmp_asc(const void *a, const void *b) {
     int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
-    float x = g_sort_sig[i], y = g_sort_sig[j];
-    if (x < y) return -1;
-    if (x > y) return 1;
+    int c = sig_order(g_sort_sig[i], g_sort_sig[j], 0);
+    if (c) return c;
     return (i > j) - (i < j);
 }
 
-static void rank_select(const float *s, int64_t n, double frac, int desc, uint8_t *mark) {
+/* the k = ceil(frac n) first leaves in the selection order; with ties, also every leaf whose
+ * signal compares equal to the k-th (a threshold at the k-th value) */
+static void rank_select(const float *s, int64_t n, double frac, int desc, int ties, uint8_t *mark) {
     int64_t k = (int64_t)ceil(frac * (double)n);
     if (k > n) k = n;
     if (k < 0) k = 0;
@@ -454,6 +463,11 @@ static void rank_select(const float *s, int64_t n, double frac, int desc, uint8_
     if (n > 1) qsort(idx, (size_t)n, sizeof(int64_t), desc ? cmp_desc : cmp_asc);
     for (int64_t i = 0; i < n; i++) mark[i] = 0;
     for (int64_t i = 0; i < k; i++) mark[idx[i]] = 1;
+    if (ties && k > 0) {
+        float kth = s[idx[k - 1]];
+        for (int64_t i = 0; i < n; i++)
+            if (sig_order(s[i], kth, desc) == 0) mark[i] = 1;
+    }
     free(idx);
 }
 
@@ -462,10 +476,10 @@ int oracle_select(const float *s, int64_t n, int32_t prune_mode, double prune_va
                   uint8_t *sample_mark) {
     if (prune_mode == 0) memset(prune_mark, 0, (size_t)n);
     else if (prune_mode == 1) { float thr = (float)prune_value; for (int64_t i = 0; i < n; i++) prune_mark[i] = s[i] <= thr; }
-    else rank_select(s, n, prune_value, 0, prune_mark);
+    else rank_select(s, n, prune_value, 0, prune_mode == 3, prune_mark);
     if (sample_mode == 0) memset(sample_mark, 0, (size_t)n);
     else if (sample_mode == 1) { float thr = (float)sample_value; for (int64_t i = 0; i < n; i++) sample_mark[i] = s[i] > thr; }
-    else rank_select(s, n, sample_value, 1, sample_mark);
+    else rank_select(s, n, sample_value, 1, sample_mode == 3, sample_mark);
     return 0;
 }
 

@@ -61,7 +61,9 @@ int oracle_backward(const otree *t, const oopts *op, const double *sigma, const 
 
 /* selection: mode 1 threshold (prune: S <= thr, sample: S > thr), mode 2 rank fraction
  * (prune: the ceil(f L) smallest by (S asc, id asc); sample: the ceil(f L) largest by
- * (S desc, id asc)). */
+ * (S desc, id asc)), mode 3 quantile (mode 2 plus every leaf whose signal equals the last one
+ * taken).  Signals compare as IEEE floats (-0 equals +0); a NaN is never marked by a
+ * threshold and comes after every number in both rank orders. */
 int oracle_select(const float *signal, int64_t n, int32_t prune_mode, double prune_value,
                   int32_t sample_mode, double sample_value, uint8_t *prune_mark,
                   uint8_t *sample_mark);

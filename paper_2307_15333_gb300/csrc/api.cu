@@ -528,10 +528,10 @@ int dot_select_masks(const dot_tree *t, const float *signal, const dot_select_op
     if (!opts) return fail(DOT_ERR_INVALID_ARG, "opts is NULL");
     const int64_t L = t->a.n_leaves;
     for (int m : {opts->prune_mode, opts->sample_mode})
-        if (m < DOT_SELECT_NONE || m > DOT_SELECT_FRACTION)
+        if (m < DOT_SELECT_NONE || m > DOT_SELECT_QUANTILE)
             return fail(DOT_ERR_INVALID_ARG, "unknown selection mode");
-    if ((opts->prune_mode == DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
-        (opts->sample_mode == DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
+    if ((opts->prune_mode >= DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
+        (opts->sample_mode >= DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
         return fail(DOT_ERR_INVALID_ARG, "selection fraction must be in [0, 1]");
     if (L > 0 && (!signal || !prune_mark || !sample_mark))
         return fail(DOT_ERR_INVALID_ARG, "signal and masks must not be NULL");
@@ -633,10 +633,10 @@ extern "C" int dot_select_masks_noalloc(const dot_tree *t, const float *signal,
         return fail(DOT_ERR_INVALID_ARG,
                     "dot_select_masks_noalloc handles at most 2^26 leaves; use dot_select_masks");
     for (int m : {opts->prune_mode, opts->sample_mode})
-        if (m < DOT_SELECT_NONE || m > DOT_SELECT_FRACTION)
+        if (m < DOT_SELECT_NONE || m > DOT_SELECT_QUANTILE)
             return fail(DOT_ERR_INVALID_ARG, "unknown selection mode");
-    if ((opts->prune_mode == DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
-        (opts->sample_mode == DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
+    if ((opts->prune_mode >= DOT_SELECT_FRACTION && !(opts->prune_value >= 0.0 && opts->prune_value <= 1.0)) ||
+        (opts->sample_mode >= DOT_SELECT_FRACTION && !(opts->sample_value >= 0.0 && opts->sample_value <= 1.0)))
         return fail(DOT_ERR_INVALID_ARG, "selection fraction must be in [0, 1]");
     if (L > 0 && (!signal || !prune_mark || !sample_mark))
         return fail(DOT_ERR_INVALID_ARG, "signal and masks must not be NULL");

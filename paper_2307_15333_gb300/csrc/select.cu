@@ -4,7 +4,8 @@
 // (sample) signals with ties broken by ascending leaf id: the k-th key is found by a 4-pass radix
 // select over order-preserving 32-bit keys (256-bin histograms, all on the device), then keys
 // below it are taken and keys equal to it are taken in id order up to the remaining count (an
-// exclusive scan of the equality flags).
+// exclusive scan of the equality flags).  Quantile mode takes every key up to and including the
+// k-th (no scan).
 #include "internal.cuh"
 #include "tree.cuh"
 
@@ -20,9 +21,11 @@ struct SelState {
 
 // order-preserving key: smaller key = earlier in the selection order
 __device__ __forceinline__ unsigned sel_key(float s, bool largest_first) {
-    const unsigned u = __float_as_uint(s);
+    unsigned u = __float_as_uint(s);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0xffffffffu;  // NaN: after every number
+    if (u == 0x80000000u) u = 0u;                             // -0 is the same value as +0
     const unsigned a = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return largest_first ? ~a : a;
+    return largest_first ? ~a : a;  // a number's key never reaches 0xffffffff
 }
 
 __global__ void hist_kernel(const float *__restrict__ sig, int64_t n, bool largest_first,
@@ -65,15 +68,16 @@ __global__ void pick_kernel(unsigned *__restrict__ hist, SelState *__restrict__ 
     hist[threadIdx.x] = 0;
 }
 
+// ties: every key equal to the selected one is taken too (quantile mode; eq is not written)
 __global__ void mark_lt_kernel(const float *__restrict__ sig, int64_t n, bool largest_first,
-                               const SelState *__restrict__ st, uint8_t *__restrict__ mark,
-                               int32_t *__restrict__ eq) {
+                               const SelState *__restrict__ st, bool ties,
+                               uint8_t *__restrict__ mark, int32_t *__restrict__ eq) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned k = sel_key(__ldg(sig + i), largest_first);
     const unsigned v = st->prefix;
-    mark[i] = k < v ? 1 : 0;
-    eq[i] = k == v ? 1 : 0;
+    mark[i] = (k < v || (ties && k == v)) ? 1 : 0;
+    if (!ties) eq[i] = k == v ? 1 : 0;
 }
 
 __global__ void mark_eq_kernel(const int32_t *__restrict__ eq, const int32_t *__restrict__ rank,
@@ -107,7 +111,7 @@ __global__ void threshold_kernel(const float *__restrict__ sig, int64_t n, bool 
         if (e_ != cudaSuccess) return e_;      \
     } while (0)
 
-cudaError_t rank_select(const float *sig, int64_t n, int64_t k, bool largest_first,
+cudaError_t rank_select(const float *sig, int64_t n, int64_t k, bool largest_first, bool ties,
                         uint8_t *mark, cudaStream_t s) {
     if (k <= 0) return cudaMemsetAsync(mark, 0, (size_t)n, s);
     if (k >= n) return cudaMemsetAsync(mark, 1, (size_t)n, s);
@@ -135,11 +139,17 @@ cudaError_t rank_select(const float *sig, int64_t n, int64_t k, bool largest_fir
         pick_kernel<<<1, 256, 0, s>>>(hist, st, shift);
     }
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    mark_lt_kernel<<<blocks, 256, 0, s>>>(sig, n, largest_first, st, mark, eq);
-    SEL_CK(scan_exclusive_i32(eq, rank, n, (int32_t *)(scratch + off_total), scratch + off_scan, s));
-    mark_eq_kernel<<<blocks, 256, 0, s>>>(eq, rank, n, st, mark);
-    SEL_CK(cudaGetLastError());
-    return cudaFreeAsync(scratch, s);
+    mark_lt_kernel<<<blocks, 256, 0, s>>>(sig, n, largest_first, st, ties, mark, eq);
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && !ties)
+        err = scan_exclusive_i32(eq, rank, n, (int32_t *)(scratch + off_total), scratch + off_scan, s);
+    if (err == cudaSuccess && !ties) {
+        mark_eq_kernel<<<blocks, 256, 0, s>>>(eq, rank, n, st, mark);
+        err = cudaGetLastError();
+    }
+    // the scratch goes back on every path once it is allocated; the first error is reported
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
+    return err != cudaSuccess ? err : ef;
 }
 
 cudaError_t one_mask(const float *sig, int64_t n, int mode, double value, bool prune,
@@ -152,7 +162,7 @@ cudaError_t one_mask(const float *sig, int64_t n, int mode, double value, bool p
     }
     double kk = ceil(value * (double)n);
     int64_t k = kk < 0 ? 0 : (kk > (double)n ? n : (int64_t)kk);
-    return rank_select(sig, n, k, !prune, mark, s);
+    return rank_select(sig, n, k, !prune, mode == DOT_SELECT_QUANTILE, mark, s);
 }
 
 }  // namespace

@@ -37,9 +37,11 @@ struct NaScratch {
 static __device__ __align__(256) NaScratch g_select_scratch;
 
 __device__ __forceinline__ unsigned na_key(float s, bool largest_first) {
-    const unsigned u = __float_as_uint(s);
+    unsigned u = __float_as_uint(s);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0xffffffffu;  // NaN: after every number
+    if (u == 0x80000000u) u = 0u;                             // -0 is the same value as +0
     const unsigned a = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return largest_first ? ~a : a;
+    return largest_first ? ~a : a;  // a number's key never reaches 0xffffffff
 }
 
 __global__ void na_init_kernel(NaScratch *sc, long long k) {
@@ -117,10 +119,11 @@ __device__ __forceinline__ int32_t na_block_scan(int32_t v, int32_t *total) {
     return base + inc - v;
 }
 
-// marks keys below the selected key; counts the tile's keys equal to it
+// marks keys below the selected key (and equal to it with ties, quantile mode); counts the
+// tile's keys equal to it
 __global__ void __launch_bounds__(kTileThreads)
-na_mark_lt_kernel(const float *__restrict__ sig, int64_t n, bool largest_first, NaScratch *sc,
-                  uint8_t *__restrict__ mark) {
+na_mark_lt_kernel(const float *__restrict__ sig, int64_t n, bool largest_first, bool ties,
+                  NaScratch *sc, uint8_t *__restrict__ mark) {
     const unsigned v = sc->st.prefix;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kTileItems;
     int32_t eq = 0;
@@ -129,7 +132,7 @@ na_mark_lt_kernel(const float *__restrict__ sig, int64_t n, bool largest_first, 
         const int64_t idx = base + i;
         if (idx < n) {
             const unsigned k = na_key(__ldg(sig + idx), largest_first);
-            mark[idx] = k < v ? 1 : 0;
+            mark[idx] = (k < v || (ties && k == v)) ? 1 : 0;
             eq += k == v;
         }
     }
@@ -192,21 +195,29 @@ __global__ void na_fill_kernel(uint8_t *__restrict__ mark, int64_t n, uint8_t va
     if (i < n) mark[i] = value;
 }
 
-// device address of the scratch, looked up once per device with that device current
+// Device address of the scratch.  Outside stream capture it is looked up on every call with the
+// calling device current, so a context destroyed and created again (cudaDeviceReset) never
+// leaves a stale address behind; the last address seen on each device is kept for calls made
+// while their stream is being captured, where the lookup is not repeated.
 std::mutex g_addr_mutex;
 NaScratch *g_addr[64] = {nullptr};
 
-cudaError_t scratch_address(NaScratch **out) {
+cudaError_t scratch_address(cudaStream_t s, NaScratch **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_select_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = reinterpret_cast<NaScratch *>(p);
+    } else if (!g_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;  // no call on this device before the capture
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -242,9 +253,12 @@ cudaError_t na_one_mask(NaScratch *sc, const float *sig, int64_t n, int mode, do
         na_pick_kernel<<<1, 256, 0, s>>>(sc, shift);
     }
     const int n_tiles = (int)((n + kTile - 1) / kTile);
-    na_mark_lt_kernel<<<n_tiles, kTileThreads, 0, s>>>(sig, n, largest_first, sc, mark);
-    na_scan_tiles_kernel<<<1, kTileThreads, 0, s>>>(sc, n_tiles);
-    na_mark_eq_kernel<<<n_tiles, kTileThreads, 0, s>>>(sig, n, largest_first, sc, mark);
+    const bool ties = mode == DOT_SELECT_QUANTILE;
+    na_mark_lt_kernel<<<n_tiles, kTileThreads, 0, s>>>(sig, n, largest_first, ties, sc, mark);
+    if (!ties) {
+        na_scan_tiles_kernel<<<1, kTileThreads, 0, s>>>(sc, n_tiles);
+        na_mark_eq_kernel<<<n_tiles, kTileThreads, 0, s>>>(sig, n, largest_first, sc, mark);
+    }
     return cudaGetLastError();
 }
 
@@ -256,7 +270,7 @@ cudaError_t select_masks_noalloc(const float *signal, int64_t n, int prune_mode,
                                  double prune_value, int sample_mode, double sample_value,
                                  uint8_t *prune_mark, uint8_t *sample_mark, cudaStream_t s) {
     NaScratch *sc = nullptr;
-    cudaError_t e = scratch_address(&sc);
+    cudaError_t e = scratch_address(s, &sc);
     if (e != cudaSuccess) return e;
     e = na_one_mask(sc, signal, n, prune_mode, prune_value, true, prune_mark, s);
     if (e != cudaSuccess) return e;

@@ -28,7 +28,7 @@ DOT_ERR_UNSUPPORTED = -5
 DOT_STORAGE_F32, DOT_STORAGE_F16, DOT_STORAGE_BF16 = 0, 1, 2
 DOT_ACT_SIGMOID, DOT_ACT_LINEAR = 0, 1
 DOT_SIGNAL_NONE, DOT_SIGNAL_SUM_ALPHA, DOT_SIGNAL_MAX_WEIGHT, DOT_SIGNAL_SIGMA = 0, 1, 2, 3
-DOT_SELECT_NONE, DOT_SELECT_THRESHOLD, DOT_SELECT_FRACTION = 0, 1, 2
+DOT_SELECT_NONE, DOT_SELECT_THRESHOLD, DOT_SELECT_FRACTION, DOT_SELECT_QUANTILE = 0, 1, 2, 3
 DOT_MERGE_MEAN, DOT_MERGE_SUM, DOT_MERGE_MAX = 0, 1, 2
 DOT_RAYS_BUFFER, DOT_RAYS_CAMERAS = 0, 1
 DOT_PRECISION_AUTO, DOT_PRECISION_FAST, DOT_PRECISION_EXACT = 0, 1, 2

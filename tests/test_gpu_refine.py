@@ -27,7 +27,8 @@ def test_select_sizes(D):
     pm = torch.empty(L, dtype=torch.uint8, device="cuda")
     sm = torch.empty(L, dtype=torch.uint8, device="cuda")
     for (pmode, pval, smode, sval) in [(2, 0.0, 2, 0.01), (2, 0.2, 2, 0.05), (2, 1.0, 2, 1.0),
-                                       (1, 0.3, 1, 2.0), (2, 0.5, 0, 0.0), (0, 0.0, 2, 0.999)]:
+                                       (1, 0.3, 1, 2.0), (2, 0.5, 0, 0.0), (0, 0.0, 2, 0.999),
+                                       (3, 0.2, 3, 0.05), (3, 0.0, 3, 1.0), (3, 0.9, 2, 0.3)]:
         dot.dot_select_masks(tree, sig, dot.select_opts(pmode, pval, smode, sval), pm, sm)
         rp, rs = oracle.select(s, pmode, pval, smode, sval)
         np.testing.assert_array_equal(pm.cpu().numpy(), rp)
@@ -153,4 +154,41 @@ def test_sample_by_copy_keeps_pixels_on_gpu():
     b = torch.empty_like(a)
     dot.dot_render_forward(tree, rays, opts, b)
     torch.testing.assert_close(b, a, rtol=2e-5, atol=2e-6)
+    tree.free()
+
+
+@pytest.mark.parametrize("entry", ["dot_select_masks", "dot_select_masks_noalloc"])
+@pytest.mark.parametrize("D", [3, 6])
+def test_select_signed_zeros_and_nan_match_oracle(entry, D):
+    """Rank boundaries inside a run of mixed +0.0 / -0.0 signals, and fractions large enough to
+    reach the NaNs: both selection calls give the oracle's marks bit for bit (-0 equals +0, a NaN
+    comes after every number in both orders, equal keys go in leaf-id order)."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.box_scene((-2, -2, -2), (2, 2, 2), max_depth=D, sh_degree=0)
+    tree = _tree(scene)
+    L = tree.n_leaves
+    s = si.signed_signal(L, 40 + D)
+    neg_zero = np.signbit(s) & (s == 0)
+    assert neg_zero.any() and ((s == 0) & ~neg_zero).any() and np.isnan(s).any()
+    sig = torch.from_numpy(s).cuda()
+    pm = torch.empty(L, dtype=torch.uint8, device="cuda")
+    sm = torch.empty(L, dtype=torch.uint8, device="cuda")
+    n_neg, n_pos = int((s < 0).sum()), int((s > 0).sum())
+    n_num = L - int(np.isnan(s).sum())
+    # bottom fraction ending inside the zeros; top fraction ending inside the zeros; NaNs reached
+    f_bot = (n_neg + 0.5 * int((s == 0).sum())) / L
+    f_top = (n_pos + 0.5 * int((s == 0).sum())) / L
+    f_nan = (n_num + 0.5 * (L - n_num)) / L
+    call = getattr(dot.dot, entry)
+    for (pmode, pval, smode, sval) in [(2, f_bot, 2, f_top), (2, f_nan, 2, f_nan),
+                                       (1, 0.0, 1, -0.0), (1, -0.0, 1, 0.0), (2, 1.0, 2, 0.999),
+                                       (3, f_bot, 3, f_top), (3, f_nan, 3, f_nan)]:
+        call(tree, sig, dot.select_opts(pmode, pval, smode, sval), pm, sm)
+        rp, rs = oracle.select(s, pmode, pval, smode, sval)
+        np.testing.assert_array_equal(pm.cpu().numpy(), rp)
+        np.testing.assert_array_equal(sm.cpu().numpy(), rs)
+    # the bottom boundary did fall among the zeros, with both signs on either side of it
+    rp, _ = oracle.select(s, 2, f_bot, 0, 0.0)
+    z = s == 0
+    assert rp[z].any() and not rp[z].all()
     tree.free()

@@ -181,6 +181,67 @@ def test_select_threshold_and_rank():
         np.testing.assert_array_equal(pm, e)
 
 
+def _brute_rank_marks(s, frac, desc, ties=False):
+    """Marks of the ceil(frac n) first leaves in the selection order, by a plain Python sort:
+    NaN after every number, -0.0 == +0.0 (Python float equality), then leaf id.  With ties, also
+    every leaf whose (NaN flag, value) equals the k-th one's."""
+    n = len(s)
+    k = int(np.ceil(frac * n))
+
+    def key(i):
+        x = float(s[i])
+        if x != x:
+            return (1, 0.0, i)
+        return (0, -x if desc else x, i)
+    order = sorted(range(n), key=key)
+    m = np.zeros(n, np.uint8)
+    m[order[:k]] = 1
+    if ties and k > 0:
+        last = key(order[k - 1])[:2]
+        for i in range(n):
+            if key(i)[:2] == last:
+                m[i] = 1
+    return m
+
+
+def test_select_signed_zeros_and_nan():
+    """Signed zeros are one value and a NaN sorts last in both directions; a k-th boundary that
+    falls inside a run of mixed +0.0 / -0.0 signals is filled in leaf-id order."""
+    rng = np.random.default_rng(3)
+    n = 400
+    s = rng.exponential(1.0, n).astype(np.float32)
+    zeros = rng.choice(n, 120, replace=False)
+    s[zeros] = np.where(rng.random(120) < 0.5, np.float32(-0.0), np.float32(0.0))
+    rest = np.setdiff1d(np.arange(n), zeros)
+    s[rng.choice(rest, 9, replace=False)] = np.nan
+    assert np.any(np.signbit(s) & (s == 0)) and np.any(~np.signbit(s) & (s == 0))
+    for frac in (0.1, 0.2, 0.3, 0.5, 0.98, 1.0):
+        pm, sm = oracle.select(s, oracle.SELECT_FRACTION, frac, oracle.SELECT_FRACTION, frac)
+        np.testing.assert_array_equal(pm, _brute_rank_marks(s, frac, False))
+        np.testing.assert_array_equal(sm, _brute_rank_marks(s, frac, True))
+        pm, sm = oracle.select(s, oracle.SELECT_QUANTILE, frac, oracle.SELECT_QUANTILE, frac)
+        np.testing.assert_array_equal(pm, _brute_rank_marks(s, frac, False, ties=True))
+        np.testing.assert_array_equal(sm, _brute_rank_marks(s, frac, True, ties=True))
+    # the bottom 10% / 20% boundary lies inside the 120 zeros: both signs are taken by id
+    pm, _ = oracle.select(s, oracle.SELECT_FRACTION, 0.2, oracle.SELECT_NONE, 0.0)
+    zsorted = np.sort(zeros)
+    np.testing.assert_array_equal(np.flatnonzero(pm), zsorted[:80])
+    # a NaN is never marked by a threshold, and is picked last by a rank selection
+    pm, sm = oracle.select(s, oracle.SELECT_THRESHOLD, np.inf, oracle.SELECT_THRESHOLD, -np.inf)
+    assert not np.any(pm[np.isnan(s)]) and not np.any(sm[np.isnan(s)])
+    _, sm = oracle.select(s, oracle.SELECT_NONE, 0.0, oracle.SELECT_FRACTION, (n - 9) / n)
+    assert not np.any(sm[np.isnan(s)]) and sm.sum() == n - 9
+    # the quantile of a boundary inside the zeros takes every zero of either sign, and the
+    # quantile prune equals a threshold at the k-th value
+    pm, _ = oracle.select(s, oracle.SELECT_QUANTILE, 0.2, oracle.SELECT_NONE, 0.0)
+    np.testing.assert_array_equal(np.flatnonzero(pm), np.sort(zeros))
+    for frac in (0.05, 0.4, 0.7):
+        k = int(np.ceil(frac * n))
+        kth = np.sort(s[~np.isnan(s)])[k - 1]
+        pm, _ = oracle.select(s, oracle.SELECT_QUANTILE, frac, oracle.SELECT_NONE, 0.0)
+        np.testing.assert_array_equal(pm, (s <= kth).astype(np.uint8))
+
+
 # ----------------------------------------------------------------------------------------------
 # recursive pruning (Sec. 3.2, Algorithm 1 with rec)
 # ----------------------------------------------------------------------------------------------
