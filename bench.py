@@ -46,9 +46,16 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true",
                    help="skip the training-loop and Tanks&Temples-shaped measurements")
-    p.add_argument("--serve-requests", type=int, default=1000,
-                   help="requests per serving trace at 200 req/s (twice as many at 2000 req/s)")
-    return p.parse_args()
+    p.add_argument("--serve-seconds", type=float, default=20.0,
+                   help="length of each serving trace (Poisson arrivals at 200 and 2000 req/s)")
+    p.add_argument("--serve-repeats", type=int, default=3,
+                   help="serving traces per rate and server (other seeds)")
+    p.add_argument("--serve-requests", type=int, default=None,
+                   help="shorthand for traces of this many requests at 200 req/s, one repeat")
+    a = p.parse_args()
+    if a.serve_requests is not None:
+        a.serve_seconds, a.serve_repeats = a.serve_requests / 200.0, 1
+    return a
 
 
 # ----------------------------------------------------------------------------------------------
@@ -225,36 +232,56 @@ def oracle_baseline(scene, cams, budget_s: float, threads: int, sampler=None):
             "sample": f"{desc} ({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
 
 
-def measure_serving(args):
-    """Continuous batching (slot tables replayed as CUDA graphs, two in flight) against one
-    launch per request, on the same seeded Poisson traces over four resident trees."""
+def measure_serving(args, refined_tree):
+    """Continuous batching (slot tables replayed as CUDA graphs, two in flight; one slot launch
+    per storage / SH-degree group of the trees, on forked streams) against one launch per
+    request, on the same seeded Poisson traces over the four resident trees: the tiny FP32 SH-1
+    scene, the tree the training run left after its refines, and two seed variants of the
+    NeRF-synthetic-shaped scene (FP16, SH degree 3).  Each rate runs several traces (other
+    seeds) through both servers."""
     import torch
 
     import seeded_inputs as si
     import paper_2307_15333_gb300 as dot
     from paper_2307_15333_gb300 import serve
-    scenes, poses = si.config_serving()
-    trees = [dot.octree_from_scene(s) for s in scenes]
+    scenes, refined, poses = si.config_serving()
+    trees = [refined_tree if ref else dot.octree_from_scene(s) for s, ref in zip(scenes, refined)]
     opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
     free, _ = torch.cuda.mem_get_info()
     pool_floats = int(min(free // 8, 1 << 28))            # admission pool: an eighth of free HBM
-    res = {"trees": [s.name for s in scenes], "leaves": [t.n_leaves for t in trees],
+    res = {"trees": [s.name + (" (after training refines)" if r else "") for s, r in zip(scenes, refined)],
+           "leaves": [t.n_leaves for t in trees],
+           "storage_sh_degree": [[int(t.storage), int(t.sh_degree)] for t in trees],
+           "slot_groups": serve.slot_groups(trees),
            "resolutions": si.SERVE_RESOLUTIONS, "pool_MB": pool_floats * 4 / 1e6,
+           "trace_seconds": args.serve_seconds, "repeats": args.serve_repeats,
            "latency": "arrival to completion observed by the host loop"}
-    for rate, n in ((200.0, args.serve_requests), (2000.0, 2 * args.serve_requests)):
-        row = {}
-        for mode, cls in (("batched", serve.BatchedServer), ("plain", serve.PlainServer)):
-            srv = cls(trees, opts, pool_floats)
-            srv.run(serve.poisson_trace(50, rate, 4, si.SERVE_RESOLUTIONS, poses, seed=1))
-            trace = serve.poisson_trace(n, rate, 4, si.SERVE_RESOLUTIONS, poses, seed=2)
-            torch.cuda.synchronize()
-            srv.run(trace)
-            rays = sum(r.width * r.height for r in trace)
-            span = max(r.done for r in trace) - trace[0].arrival
-            row[mode] = dict(serve.percentiles(trace), mrays_s=rays / span / 1e6, requests=n)
-            del srv
-            torch.cuda.synchronize()
+    servers = {"batched": serve.BatchedServer(trees, opts, pool_floats),
+               "plain": serve.PlainServer(trees, opts, pool_floats)}
+    for srv in servers.values():                          # warm-up
+        srv.run(serve.poisson_trace(50, 200.0, 4, si.SERVE_RESOLUTIONS, poses, seed=1))
+    torch.cuda.synchronize()
+    for rate in (200.0, 2000.0):
+        n = int(rate * args.serve_seconds)
+        runs = {"batched": [], "plain": []}
+        for rep in range(args.serve_repeats):
+            for mode in ("batched", "plain") if rep % 2 == 0 else ("plain", "batched"):
+                trace = serve.poisson_trace(n, rate, 4, si.SERVE_RESOLUTIONS, poses, seed=2 + rep)
+                torch.cuda.synchronize()
+                servers[mode].run(trace)
+                rays = sum(r.width * r.height for r in trace)
+                span = max(r.done for r in trace) - trace[0].arrival
+                runs[mode].append(dict(serve.percentiles(trace), mrays_s=rays / span / 1e6,
+                                       requests=n, seed=2 + rep))
+        ratio = [b["p99_ms"] / p["p99_ms"] for b, p in zip(runs["batched"], runs["plain"])]
+        row = {m: {"runs": r,
+                   "p50_ms": [x["p50_ms"] for x in r], "p99_ms": [x["p99_ms"] for x in r],
+                   "mrays_s": [x["mrays_s"] for x in r]} for m, r in runs.items()}
+        row["batched_over_plain_p99"] = {"each": ratio, "min": min(ratio), "max": max(ratio)}
+        row["batched_p99_below_plain_every_run"] = all(x < 1.0 for x in ratio)
         res[f"rate_{int(rate)}_per_s"] = row
+    del servers
+    torch.cuda.synchronize()
     for t in trees:
         t.free()
     return res
@@ -365,6 +392,76 @@ def measure_training(scene, cams, steps: int):
            "iters_per_s_with_refine_every_1000": 1000.0 / ((1000 * ms / n + refine_ms) / 1e3)}
     tree.free()
     return out
+
+
+def measure_train_config3(iters: int = 3000, refine_every: int = 1000, keep_tree: bool = False):
+    """Algorithm 1 on the differentiable-training configuration as specified: the tiny sphere
+    scene (depth 4, FP32 leaves, SH degree 1) trained toward targets rendered from a seeded
+    perturbed copy of its parameters (density x U(0.8, 1.2), SH + N(0, 0.1)), on 2^16-ray
+    batches drawn from its 100 views of 800x800 (a pool of 100 batches, one epoch = one pass
+    over them in a permuted order), with the fused training step, the MAX_WEIGHT signal and a
+    refine every 1000 iterations (leaves at or below the 20% quantile of the signal
+    prune-marked, top 5% sampled, depth cap D + 2), all through Trainer.fit.  Reports iterations/s, the time of each refine, the
+    leaves after each, and the loss curve (mean batch MSE of every epoch).  Returns (result, the
+    trained tree if keep_tree else None)."""
+    import torch
+
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.train import Trainer
+    scene, cams = si.config_train()
+    tree = dot.octree_from_scene(scene)
+    ex = tree.export()
+    sg, shg = si.perturbed_params(ex["sigma"], ex["sh"], seed=2002)
+    goal = dot.dot.dot_tree_import(dict(ex, sigma=sg, sh=shg))
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+    pool = 100
+    batches, keep = [], []
+    for i in range(pool):
+        o, d = si.ray_batch(cams, BATCH, seed=20000 + i)
+        ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+        r = dot.rays_buffer(ot, dt)
+        t = torch.empty(BATCH, 3, device="cuda")
+        dot.dot_render_forward(goal, r, opts, t)
+        batches.append((r, t))
+        keep.append((ot, dt))
+    torch.cuda.synchronize()
+    goal.free()
+    rng = np.random.default_rng(2003)
+
+    def epoch(i):
+        return [batches[j] for j in rng.permutation(pool)]
+    tr = Trainer(tree, opts, dot.dot.rmsprop_opts(), signal_mode=dot.dot.DOT_SIGNAL_MAX_WEIGHT)
+    leaves = [tree.n_leaves]
+    pruned = []
+
+    def on_refine(i, plan):
+        leaves.append(plan["n_leaves"])
+        pruned.append(sum(p["n_pruned_groups"] for p in plan["passes"]))
+    F = dot.dot.DOT_SELECT_FRACTION
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = tr.fit(epoch, epochs=iters // pool, T=refine_every // pool, tau=0.2, gamma=0.05,
+                    depth_cap=scene.max_depth + 2, recursive=False,
+                    prune_mode=dot.dot.DOT_SELECT_QUANTILE, sample_mode=F, on_refine=on_refine)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    assert tree.status() == 0
+    step_s = wall - sum(tr.refine_ms) / 1e3
+    out = {"workload": "tiny_sphere_d4_sh1_f32_train_100x800x800", "batch_rays": BATCH,
+           "iters": iters, "refine_every": refine_every, "refines": len(tr.refine_ms),
+           "iters_per_s": iters / step_s, "iters_per_s_with_refines": iters / wall,
+           "refine_ms": tr.refine_ms, "leaves_after_each_refine": leaves,
+           "loss_per_epoch": losses, "epoch_iters": pool,
+           "loss_first_last": [losses[0], losses[-1]],
+           "targets": "render of a perturbed copy (density x U(0.8,1.2), SH + N(0,0.1), seed 2002)",
+           "step": "fused fwd + MSE grad + bwd, MAX_WEIGHT signal, sparse RMSProp",
+           "select": "prune at the 20% quantile of the signal, sample top 5% (rank), depth cap 6",
+           "pruned_groups_per_refine": pruned}
+    if not keep_tree:
+        tree.free()
+        tree = None
+    return out, tree
 
 
 def measure_compressed(scene, cams, steps: int):
@@ -728,8 +825,14 @@ def run_dot(args):
                                          "canonicalize_ms": canon_ms}
     del rgb2, perm
 
-    serve_res = measure_serving(args) if rank == 0 else None
     train_res = measure_training(scene, cams, args.steps) if rank == 0 and not args.quick else None
+    train3_res, serve_res = None, None
+    if rank == 0:
+        # the training configuration's run (a shorter one with --quick) leaves the refined tree
+        # that the serving measurement keeps resident
+        train3_res, trained = (measure_train_config3(keep_tree=True) if not args.quick else
+                               measure_train_config3(iters=300, refine_every=100, keep_tree=True))
+        serve_res = measure_serving(args, trained)
     tt_res = measure_tanks_temples(args.steps) if rank == 0 and not args.quick else None
     comp_res = measure_compressed(scene, cams, args.steps) if rank == 0 and not args.quick else None
 
@@ -771,6 +874,7 @@ def run_dot(args):
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "train": train_res,
+            "train_config3": train3_res,
             "tanks_temples": tt_res, "compressed": comp_res, "serve": serve_res,
             "wall_s_timed": t_wall}
     if rank == 0:

@@ -4,9 +4,13 @@ Requests (a tree, a camera pose, a resolution) arrive over time.  The batched se
 waiting requests into free slots whenever a slot table is free and the output pool has room,
 packs them into a slot table (16x8 tiles of every request numbered consecutively), and replays a
 CUDA graph captured once per table: host-to-device copy of the table, then dot_render_slots (one
-persistent launch that drains the tiles of all admitted requests).  Two tables are in flight at
-a time on two streams, so requests that arrive while a batch is on the GPU start in the next one
-at once and their work overlaps on the device.  The plain server launches dot_render_forward once
+persistent launch that drains the tiles of all admitted requests).  Resident trees that differ in
+storage type, SH degree or compression cannot share one slot launch (each is a different build
+of the march), so the trees are split into groups that can, a table holds one sub-table per
+group, and the graph runs one slot launch per group on forked streams that join again: one
+replay renders a mixed batch, and the groups' launches overlap on the device.  Two tables are in
+flight at a time on two streams, so requests that arrive while a batch is on the GPU start in the
+next one at once and their work overlaps on the device.  The plain server launches dot_render_forward once
 per request, in arrival order, on one stream.
 
 Host bookkeeping (pool, packing, trace) is plain Python and runs without a GPU; only
@@ -85,15 +89,33 @@ class OutputPool:
         return sum(l for _, l in self.free)
 
 
-def pack_table(reqs: Sequence[Request], pool_base_ptr: int, max_slots: int) -> np.ndarray:
-    """Byte image of a slot table: header then one 96-byte dot_slot per request."""
+def slot_groups(trees) -> List[List[int]]:
+    """Indices of the trees grouped by what one slot launch can serve together (storage type, SH
+    degree, compressed or not), groups in order of first appearance.  Each tree is any object
+    with storage, sh_degree and palette_bits attributes."""
+    keys: List[tuple] = []
+    groups: List[List[int]] = []
+    for i, t in enumerate(trees):
+        k = (int(t.storage), int(t.sh_degree), int(t.palette_bits) > 0)
+        if k not in keys:
+            keys.append(k)
+            groups.append([])
+        groups[keys.index(k)].append(i)
+    return groups
+
+
+def pack_table(reqs: Sequence[Request], pool_base_ptr: int, max_slots: int,
+               tree_index=None) -> np.ndarray:
+    """Byte image of a slot table: header then one 96-byte dot_slot per request.  tree_index
+    maps a request's tree to its index in the launch's tree list (identity if None)."""
     assert len(reqs) <= max_slots
     buf = np.zeros(HEADER_BYTES + SLOT_BYTES * max_slots, dtype=np.uint8)
     begin = 0
     for i, r in enumerate(reqs):
         rec = buf[HEADER_BYTES + SLOT_BYTES * i: HEADER_BYTES + SLOT_BYTES * (i + 1)]
         rec[0:72] = np.ascontiguousarray(r.camera, dtype=np.float32).view(np.uint8)
-        rec[72:76] = np.array([r.tree], np.int32).view(np.uint8)
+        t = r.tree if tree_index is None else tree_index[r.tree]
+        rec[72:76] = np.array([t], np.int32).view(np.uint8)
         rec[80:88] = np.array([begin], np.int64).view(np.uint8)
         rec[88:96] = np.array([pool_base_ptr + 4 * r.offset], np.uint64).view(np.uint8)
         begin += r.tiles
@@ -139,12 +161,18 @@ def _no_gc_pauses():
 
 
 class _Table:
-    def __init__(self, torch, max_slots):
-        nbytes = HEADER_BYTES + SLOT_BYTES * max_slots
+    """One slot table per tree group, back to back in one pinned host buffer and one device
+    buffer (one copy per replay), a work counter per group, and the streams the group launches
+    fork onto."""
+
+    def __init__(self, torch, max_slots, n_groups):
+        self.table_bytes = HEADER_BYTES + SLOT_BYTES * max_slots
+        nbytes = self.table_bytes * n_groups
         self.host = torch.zeros(nbytes, dtype=torch.uint8, pin_memory=True)
         self.dev = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
-        self.counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.counter = torch.zeros(n_groups, dtype=torch.int64, device="cuda")
         self.stream = torch.cuda.Stream()
+        self.forks = [torch.cuda.Stream() for _ in range(n_groups - 1)]
         self.graph = None
         self.event = torch.cuda.Event()
         self.reqs: List[Request] = []
@@ -157,39 +185,62 @@ class BatchedServer:
         from . import dot
         self.torch, self.dot = torch, dot
         self.trees = list(trees)
-        self.handles = (ctypes.c_void_p * len(self.trees))(*[t.handle.value for t in self.trees])
+        self.groups = slot_groups(self.trees)
+        self.local = {}                                # tree -> (group, index in the group)
+        for g, members in enumerate(self.groups):
+            for j, t in enumerate(members):
+                self.local[t] = (g, j)
+        self.handles = [(ctypes.c_void_p * len(m))(*[self.trees[t].handle.value for t in m])
+                        for m in self.groups]
         self.opts = opts
         self.max_slots = max_slots
         self.pool_t = torch.empty(int(pool_floats), dtype=torch.float32, device="cuda")
         self.pool = OutputPool(pool_floats)
-        self.tables = [_Table(torch, max_slots) for _ in range(n_tables)]
+        self.tables = [_Table(torch, max_slots, len(self.groups)) for _ in range(n_tables)]
         for tb in self.tables:
             self._capture(tb)
 
-    def _launch(self, tb):
-        rc = self.dot.lib().dot_render_slots(self.handles, len(self.trees),
-                                             ctypes.c_void_p(tb.dev.data_ptr()), self.max_slots,
-                                             ctypes.byref(self.opts),
-                                             ctypes.c_void_p(tb.counter.data_ptr()),
-                                             ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream))
+    def _launch(self, tb, g):
+        torch = self.torch
+        rc = self.dot.lib().dot_render_slots(
+            self.handles[g], len(self.groups[g]),
+            ctypes.c_void_p(tb.dev.data_ptr() + g * tb.table_bytes), self.max_slots,
+            ctypes.byref(self.opts), ctypes.c_void_p(tb.counter.data_ptr() + 8 * g),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         if rc != 0:
             raise self.dot.DotError(rc, self.dot.dot_last_error())
+
+    def _record(self, tb):
+        """The work of one replay: the table copy, then one slot launch per group -- the first on
+        the table's stream, the others on forked streams that join it again."""
+        torch = self.torch
+        tb.dev.copy_(tb.host, non_blocking=True)
+        for g, fork in enumerate(tb.forks, start=1):
+            fork.wait_stream(tb.stream)
+            with torch.cuda.stream(fork):
+                self._launch(tb, g)
+        self._launch(tb, 0)
+        for fork in tb.forks:
+            tb.stream.wait_stream(fork)
 
     def _capture(self, tb):
         torch = self.torch
         with torch.cuda.stream(tb.stream):          # one eager run before capture
-            tb.dev.copy_(tb.host, non_blocking=True)
-            self._launch(tb)
+            self._record(tb)
         torch.cuda.synchronize()
         tb.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(tb.graph, stream=tb.stream):
-            tb.dev.copy_(tb.host, non_blocking=True)
-            self._launch(tb)
+            self._record(tb)
         torch.cuda.synchronize()
 
     def submit(self, reqs: List[Request], tb: _Table):
-        img = pack_table(reqs, self.pool_t.data_ptr(), self.max_slots)
-        tb.host.numpy()[:] = img
+        host = tb.host.numpy()
+        base = self.pool_t.data_ptr()
+        for g, members in enumerate(self.groups):
+            mine = [r for r in reqs if self.local[r.tree][0] == g]
+            index = {t: self.local[t][1] for t in members}
+            host[g * tb.table_bytes:(g + 1) * tb.table_bytes] = pack_table(
+                mine, base, self.max_slots, index)
         tb.reqs = reqs
         with self.torch.cuda.stream(tb.stream):
             tb.graph.replay()

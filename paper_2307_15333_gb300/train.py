@@ -19,6 +19,7 @@ calls.
 """
 from __future__ import annotations
 
+import time
 from typing import Callable, Iterable, List, Optional, Tuple
 
 import torch
@@ -155,8 +156,10 @@ class Trainer:
         accumulating the signal Q, then, when i is a multiple of T, pruning with tau (recursively
         when asked) and sampling the top-gamma fraction.  `on_refine(i, plan)` is called after each
         refine (the leaf numbering has changed: a caller holding per-leaf arrays remaps them with
-        self.leaf_map).  Returns the mean batch MSE of every epoch."""
+        self.leaf_map).  Returns the mean batch MSE of every epoch; the wall time of every refine
+        (device work included) is appended to self.refine_ms."""
         losses = []
+        self.refine_ms = []
         for i in range(1, epochs + 1):
             self.loss_sum.zero_()
             n = 0
@@ -165,9 +168,13 @@ class Trainer:
                 n += 1
             losses.append(float(self.loss_sum.item()) / max(n, 1))
             if i % T == 0:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
                 plan = self.refine(tau, gamma, depth_cap, recursive=recursive,
                                    prune_mode=prune_mode, sample_mode=sample_mode,
                                    canonical=canonical)
+                torch.cuda.synchronize()
+                self.refine_ms.append((time.perf_counter() - t0) * 1e3)
                 if on_refine is not None:
                     on_refine(i, plan)
         return losses

@@ -300,6 +300,14 @@ class Camera:
         out[16:18] = np.array([self.width, self.height], dtype=np.int32).view(np.float32)
         return out
 
+    @staticmethod
+    def unpack(rec: np.ndarray) -> "Camera":
+        """The camera of a packed float32[18] record (the inverse of packed())."""
+        rec = np.ascontiguousarray(rec, dtype=np.float32)
+        w, h = (int(x) for x in rec[16:18].view(np.int32))
+        return Camera(rec[:12].reshape(3, 4).copy(), w, h, float(rec[12]), float(rec[13]),
+                      float(rec[14]), float(rec[15]))
+
 
 def look_at(pos, target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0)) -> np.ndarray:
     """c2w (float32 [3,4]) of a camera at `pos` looking at `target`; x right, y up, looks down -z."""
@@ -435,6 +443,25 @@ def config_tanks_temples(n_views: int = 150):
     return sc, cams
 
 
+def config_train(n_views: int = 100):
+    """The differentiable-training configuration: the tiny sphere scene (depth 4, FP32, SH degree
+    1) and 100 views of 800x800 on a radius-3 upper hemisphere, focal 1000 (the field of view of
+    the tiny scene's own 64x64, focal-80 camera at distance 3)."""
+    sc = tiny_sphere_scene(seed=0)
+    cams = hemisphere_cameras(n_views, 3.0, 800, 800, 1000.0, seed=2001)
+    return sc, cams
+
+
+def perturbed_params(sigma: np.ndarray, sh: np.ndarray, seed: int):
+    """The seeded perturbed copy of a tree's leaf parameters that training targets are rendered
+    from: every density times U(0.8, 1.2), every SH coefficient plus N(0, 0.1), in float32 (one
+    rounding each), leaf by leaf in the given order."""
+    rng = np.random.default_rng(seed)
+    s = np.asarray(sigma, np.float32) * rng.uniform(0.8, 1.2, size=np.shape(sigma)).astype(np.float32)
+    h = np.asarray(sh, np.float32) + rng.normal(0.0, 0.1, size=np.shape(sh)).astype(np.float32)
+    return s.astype(np.float32), h.astype(np.float32)
+
+
 def random_signal(n: int, seed: int, tie_fraction: float = 0.2) -> np.ndarray:
     """Non-negative float32 signal with many exact ties (a fifth of the values repeat)."""
     rng = np.random.default_rng(seed)
@@ -444,6 +471,26 @@ def random_signal(n: int, seed: int, tie_fraction: float = 0.2) -> np.ndarray:
         idx = rng.integers(0, n, size=k)
         s[idx] = s[rng.integers(0, n, size=k)]
         s[rng.integers(0, n, size=max(1, k // 4))] = 0.0
+    return s
+
+
+def signed_signal(n: int, seed: int, p_pos: float = 0.3, p_zero: float = 0.4,
+                  p_nan: float = 0.05) -> np.ndarray:
+    """Float32 signal of positive values (a fifth of them repeated), +0.0 and -0.0 in equal
+    shares, negative values and NaNs, in random leaf order: a per-leaf signal such as raw
+    densities can hold all of these."""
+    rng = np.random.default_rng(seed)
+    u = rng.random(n)
+    s = -rng.exponential(1.0, size=n).astype(np.float32)
+    pos = u < p_pos
+    s[pos] = rng.exponential(1.0, size=int(pos.sum())).astype(np.float32)
+    idx = np.flatnonzero(pos)
+    if idx.size > 1:
+        k = idx.size // 5
+        s[rng.choice(idx, k)] = s[rng.choice(idx, k)]
+    zero = (u >= p_pos) & (u < p_pos + p_zero)
+    s[zero] = np.where(rng.random(int(zero.sum())) < 0.5, np.float32(-0.0), np.float32(0.0))
+    s[u >= 1.0 - p_nan] = np.nan
     return s
 
 
@@ -462,15 +509,18 @@ SERVE_RESOLUTIONS = [(256, 256), (512, 512), (800, 800), (1280, 720), (1920, 108
 
 
 def config_serving():
-    """Four resident scenes for the serving loop -- the NeRF-synthetic-shaped scene, the
-    Tanks&Temples-shaped scene and two seed variants of the first -- all stored FP16 with SH
-    degree 3 (one slot launch serves one storage type), and a pose sampler: a random direction on
-    the upper hemisphere at the scene's viewing distance, focal scaled with the width as in the
-    scene's own config (1111 per 800 px, 1200 per 1920 px)."""
-    scenes = [nerf_synthetic_scene(seed=1000), tanks_temples_scene(seed=3000, storage=STORAGE_F16),
+    """Four resident scenes for the serving loop: the tiny sphere scene (FP32, SH degree 1), the
+    same scene again as the tree the training configuration leaves after its refines (the caller
+    refines it: the benchmark serves the tree its training run produced, the tests refine it with
+    seeded marks), and two seed variants of the NeRF-synthetic-shaped scene (FP16, SH degree 3).
+    Also a pose sampler: a random direction on the upper hemisphere at the scene's viewing
+    distance, focal scaled with the width as in the scene's own camera (80 per 64 px for the
+    tiny scene, 1111 per 800 px for the NeRF-synthetic-shaped one)."""
+    scenes = [tiny_sphere_scene(seed=0), tiny_sphere_scene(seed=0),
               nerf_synthetic_scene(seed=1010), nerf_synthetic_scene(seed=1020)]
-    dist = [4.0, 5.0, 4.0, 4.0]
-    focal_per_px = [1111.0 / 800.0, 1200.0 / 1920.0, 1111.0 / 800.0, 1111.0 / 800.0]
+    refined = [False, True, False, False]
+    dist = [3.0, 3.0, 4.0, 4.0]
+    focal_per_px = [80.0 / 64.0, 80.0 / 64.0, 1111.0 / 800.0, 1111.0 / 800.0]
 
     def poses(rng, tree, w, h):
         y = rng.uniform(0.05, 0.95)
@@ -479,4 +529,4 @@ def config_serving():
         pos = dist[tree] * np.array([r * math.cos(phi), y, r * math.sin(phi)])
         return pinhole(pos, w, h, focal_per_px[tree] * w).packed()
 
-    return scenes, poses
+    return scenes, refined, poses

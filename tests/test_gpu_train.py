@@ -262,3 +262,126 @@ def test_fit_runs_algorithm_1():
     assert_pixels_close(got.cpu().numpy(), ref, scene.storage)
     tree.free()
     goal.free()
+
+
+def _fraction_in_gap(S, frac, largest_first):
+    """A rank fraction near `frac` whose k-th and (k+1)-th signals in the selection order are both
+    exactly zero (equal keys, taken in leaf-id order on both sides) or apart by more than 1e-4 of
+    their size, so that FP32 sums cannot move the boundary."""
+    L = S.size
+    order = np.lexsort((np.arange(L), -S if largest_first else S))
+    want = max(1, int(np.ceil(frac * L)))
+    best = None
+    for k in range(max(1, want // 2), min(L - 1, 2 * want) + 1):
+        a, b = S[order[k - 1]], S[order[k]]
+        if (a == 0 and b == 0) or abs(a - b) > 1e-4 * max(abs(a), abs(b)):
+            if best is None or abs(k - want) < abs(best - want):
+                best = k
+    assert best is not None
+    return (best - 0.5) / L
+
+
+def _quantile_in_gap(S, frac):
+    """A quantile fraction near `frac` whose bound (the k-th smallest signal) is apart from both
+    of its neighbours in sorted order by more than 1e-4 of its size, so that FP32 sums cannot
+    move a leaf across it."""
+    v = np.sort(S)
+    want = max(2, int(np.ceil(frac * S.size)))
+    best = None
+    for k in range(2, S.size):
+        a, b, c = v[k - 2], v[k - 1], v[k]
+        if b > 0 and b - a > 1e-4 * b and c - b > 1e-4 * c:
+            if best is None or abs(k - want) < abs(best - want):
+                best = k
+    assert best is not None
+    return (best - 0.5) / S.size
+
+
+def test_config3_training_matches_oracle_loop():
+    """A short run of the differentiable-training configuration: the tiny FP32 sphere scene,
+    targets rendered from the seeded perturbed copy of its parameters, batches of rays from its
+    800x800 views, two fused training steps with the MAX_WEIGHT signal, a refine (prune at a
+    quantile of the signal, then sample a top fraction of the merged signal), and two more
+    steps on the refined tree -- through Trainer on the GPU and composed from the oracle, with the
+    same targets.  Structure and leaf map bit-exact; parameters as in the other loop test."""
+    import paper_2307_15333_gb300 as dot
+    from paper_2307_15333_gb300.train import Trainer
+    scene, cams = si.config_train()
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    ex = tree.export()
+    sg, shg = si.perturbed_params(ex["sigma"], ex["sh"], seed=2002)
+    goal = dot.dot.dot_tree_import(dict(ex, sigma=sg, sh=shg))
+    bg = (1.0, 1.0, 1.0)
+    opts = dot.render_opts(background=bg, eps_T=0.0)
+    batches = []
+    for b in range(4):
+        o, d = si.ray_batch(cams, 4096, seed=600 + b)
+        tgt, _, _ = oracle.render(t, lo, size, sg.astype(np.float64), shg.astype(np.float64), 1,
+                                  o, d, bg=bg, eps_T=0.0)
+        rays = dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda())
+        # the GPU's render of the perturbed copy is the oracle's (FP32 tolerance)
+        gt = torch.empty(4096, 3, device="cuda")
+        dot.dot_render_forward(goal, rays, opts, gt)
+        torch.cuda.synchronize()
+        assert_pixels_close(gt.cpu().numpy(), tgt, si.STORAGE_F32)
+        batches.append((o, d, rays, tgt.astype(np.float32)))
+    goal.free()
+    lr_s, lr_h, rho, eps = 0.1, 0.01, 0.9, 1e-3
+    tr = Trainer(tree, opts, dot.dot.rmsprop_opts(lr_s, lr_h, rho, eps),
+                 signal_mode=dot.dot.DOT_SIGNAL_MAX_WEIGHT)
+    ms_s, ms_h = np.zeros_like(s64), np.zeros_like(h64)
+    S = np.zeros(s64.shape[0])
+
+    def oracle_step(t, s64, h64, ms_s, ms_h, S, o, d, tgt):
+        rgb, _, _ = oracle.render(t, lo, size, s64, h64, 1, o, d, bg=bg, eps_T=0.0, signal=S,
+                                  signal_mode=oracle.SIGNAL_MAX_WEIGHT)
+        _, g = oracle.mse(rgb, tgt)
+        gs, gsh, _, _ = oracle.backward(t, lo, size, s64, h64, 1, o, d, g, bg=bg, eps_T=0.0)
+        s64, ms_s = oracle.rmsprop(s64, ms_s, gs, lr_s, rho, eps)
+        h64, ms_h = oracle.rmsprop(h64, ms_h, gsh, lr_h, rho, eps)
+        return (s64.astype(np.float32).astype(np.float64),
+                h64.astype(np.float32).astype(np.float64), ms_s, ms_h)
+
+    for o, d, rays, tgt in batches[:2]:
+        tr.step(rays, torch.from_numpy(tgt).cuda())
+        s64, h64, ms_s, ms_h = oracle_step(t, s64, h64, ms_s, ms_h, S, o, d, tgt)
+    torch.cuda.synchronize()
+    assert_sums_close(tr.signal.cpu().numpy(), S, S, 1e-5, "signal")
+    # refine: prune at a quantile of the signal (placed in a gap near 0.8: on this tree every
+    # sibling group has a leaf seen by some ray, so lower quantiles merge nothing), then sample
+    # the top fraction of the merged signal
+    f_p = _quantile_in_gap(S, 0.8)
+    pm, _ = oracle.select(S.astype(np.float32), oracle.SELECT_QUANTILE, f_p)
+    nt, lm, so, sho, cnt = oracle.refine(t, s64, h64, pm, np.zeros_like(pm), scene.max_depth + 2)
+    assert cnt["n_pruned_groups"] > 0
+    S2 = oracle.remap_leaf_values(t, lm, S, "max")
+    ms_s = oracle.remap_leaf_values(t, lm, ms_s, "mean")
+    ms_h = oracle.remap_leaf_values(t, lm, ms_h, "mean")
+    f_s = _fraction_in_gap(S2, 0.05, largest_first=True)
+    _, sm = oracle.select(S2.astype(np.float32), oracle.SELECT_NONE, 0.0, oracle.SELECT_FRACTION, f_s)
+    nt2, lm2, so2, sho2, cnt = oracle.refine(nt, so, sho, np.zeros_like(sm), sm, scene.max_depth + 2)
+    assert cnt["n_sampled"] > 0
+    ms_s = oracle.remap_leaf_values(nt, lm2, ms_s, "mean")
+    ms_h = oracle.remap_leaf_values(nt, lm2, ms_h, "mean")
+    res = tr.refine(f_p, f_s, depth_cap=scene.max_depth + 2, recursive=False,
+                    prune_mode=dot.dot.DOT_SELECT_QUANTILE, sample_mode=dot.dot.DOT_SELECT_FRACTION)
+    assert res["n_leaves"] == nt2["leaf_key"].size
+    ex = tree.export()
+    for key in ("child", "node_parent", "node_key", "leaf_parent", "leaf_key"):
+        assert np.array_equal(ex[key], nt2[key]), key
+    np.testing.assert_array_equal(tr.leaf_map.cpu().numpy(), lm2)
+    # two more steps on the refined tree
+    t, s64, h64 = nt2, so2, sho2
+    S = np.zeros(s64.shape[0])
+    for o, d, rays, tgt in batches[2:]:
+        tr.step(rays, torch.from_numpy(tgt).cuda())
+        s64, h64, ms_s, ms_h = oracle_step(t, s64, h64, ms_s, ms_h, S, o, d, tgt)
+    tr.flush()
+    torch.cuda.synchronize()
+    assert tree.status() == 0
+    np.testing.assert_allclose(tree.sigma.cpu().numpy().astype(np.float64), s64, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(tree.sh.cpu().numpy().astype(np.float64), h64, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(tr.ms_sigma.cpu().numpy(), ms_s, rtol=1e-3, atol=1e-9)
+    tree.free()

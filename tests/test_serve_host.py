@@ -50,3 +50,20 @@ def test_poisson_trace_is_seeded_and_has_the_rate():
     rate = len(a) / a[-1].arrival
     assert 190 < rate < 210
     assert {r.tree for r in a} == {0, 1, 2}
+
+
+def test_slot_groups_and_per_group_tree_index():
+    """Trees that differ in storage, SH degree or compression go to different slot launches; a
+    request's slot records its tree's index within its own group."""
+    class T:
+        def __init__(self, storage, deg, bits=0):
+            self.storage, self.sh_degree, self.palette_bits = storage, deg, bits
+    trees = [T(0, 1), T(1, 3), T(0, 1), T(1, 3), T(1, 3, 16), T(2, 3)]
+    groups = serve.slot_groups(trees)
+    assert groups == [[0, 2], [1, 3], [4], [5]]
+    index = {t: j for g in groups for j, t in enumerate(g)}
+    cam = np.zeros(18, np.float32)
+    cam[16:18] = np.array([32, 16], np.int32).view(np.float32)
+    reqs = [serve.Request(i, t, 32, 16, cam, 0.0, offset=0) for i, t in enumerate([2, 0])]
+    buf = serve.pack_table(reqs, 0, 2, index)
+    assert [buf[16 + 96 * i + 72: 16 + 96 * i + 76].view(np.int32)[0] for i in range(2)] == [1, 0]
