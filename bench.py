@@ -223,6 +223,145 @@ class OracleSample:
         return time.perf_counter() - t0
 
 
+def pixel_errors(got, ref, fp32_exact: bool) -> dict:
+    """Per-ray error of GPU pixels against the oracle's: absolute, and relative to
+    max(|oracle|, 1e-2); rays beyond the stated tolerance (FP32 exact: 1e-5 relative, the
+    grazing-ray exceptions; 16-bit: 2e-3 absolute)."""
+    got = np.asarray(got, np.float64).reshape(ref.shape)
+    a = np.abs(got - ref)
+    r = a / np.maximum(np.abs(ref), 1e-2)
+    a_ray, r_ray = a.max(axis=1), r.max(axis=1)
+    beyond = r_ray > 1e-5 if fp32_exact else a_ray > 2e-3
+    return {"rays": int(ref.shape[0]), "max_abs": float(a.max()),
+            "p99_abs": float(np.percentile(a_ray, 99)), "max_rel": float(r.max()),
+            "p99_rel": float(np.percentile(r_ray, 99)),
+            "tolerance": "1e-5 relative per channel" if fp32_exact else "2e-3 absolute per channel",
+            "rays_beyond": int(beyond.sum()), "frac_beyond": float(beyond.mean())}
+
+
+def grad_errors(got, ref, absum, floor) -> dict:
+    """Error of FP32 gradient sums against the oracle's as a fraction of the 16-bit tolerance
+    (2e-3 of the entry's summed term magnitudes + floor; <= 1 is within it), and the leaves with
+    an entry beyond it."""
+    got = np.asarray(got, np.float64).reshape(ref.shape)
+    d = np.abs(got - ref)
+    live = absum > 0
+    q = d[live] / (2e-3 * absum[live] + floor)
+    bad = (d > 2e-3 * absum + floor).reshape(ref.shape[0], -1).any(axis=1)
+    n_live = int(live.reshape(ref.shape[0], -1).any(axis=1).sum())
+    return {"entries": int(live.sum()), "leaves": n_live, "floor": float(floor),
+            "max_err_over_tolerance": float(q.max()),
+            "p99_err_over_tolerance": float(np.percentile(q, 99)),
+            "leaves_beyond": int(bad.sum()), "frac_leaves_beyond": float(bad.sum() / max(n_live, 1))}
+
+
+def parity_report(threads: int, sampler=None) -> dict:
+    """Error of the GPU path against the FP64 oracle on every configuration, measured in the CPU
+    baseline leg (the oracle's own leg): the tiny FP32 scene on all 4096 pixels of its camera, the
+    NeRF-synthetic-shaped FP16 scene and the Tanks&Temples-shaped BF16 scene on seeded pixel
+    samples of their views, and the gradients of one 2^16-ray training batch of the FP16 scene
+    through the fused pass (dL/dC taken from the GPU, the backward from the oracle; rays whose
+    transmittance comes within 0.1% of eps_T are set aside, the discrete early-termination
+    decision)."""
+    import torch
+
+    import oracle
+    import seeded_inputs as si
+    import paper_2307_15333_gb300 as dot
+    out = {}
+    opts = dot.render_opts(background=(1.0, 1.0, 1.0), eps_T=1e-4)
+
+    def gpu_render(tree, o, d):
+        rgb = torch.empty(o.shape[0], 3, device="cuda")
+        dot.dot_render_forward(tree, dot.rays_buffer(torch.from_numpy(o).cuda(),
+                                                     torch.from_numpy(d).cuda()), opts, rgb)
+        torch.cuda.synchronize()
+        return rgb.cpu().numpy()
+
+    def full_params(t, sc, leaves=None):
+        if leaves is None:
+            sig, sh = si.leaf_params(t["leaf_key"], t["leaf_inside"], sc)
+            return si.storage_to_f64(sig, sc.storage), si.storage_to_f64(sh, sc.storage)
+        L = t["leaf_key"].size
+        s64 = np.zeros(L)
+        h64 = np.zeros((L, 3, sc.n_coeffs))
+        sig, sh = si.leaf_params(t["leaf_key"][leaves], t["leaf_inside"][leaves], sc)
+        s64[leaves] = si.storage_to_f64(sig, sc.storage)
+        h64[leaves] = si.storage_to_f64(sh, sc.storage)
+        return s64, h64
+
+    # tiny FP32 scene, every pixel (exact mode)
+    sc, cams = si.config_tiny()
+    tree = dot.octree_from_scene(sc)
+    t = oracle.scene_tree(sc)
+    lo, size = oracle.root_of(sc)
+    s64, h64 = full_params(t, sc)
+    o, d = si.camera_rays(cams[0])
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, sc.sh_degree, o, d, eps_T=1e-4, threads=threads)
+    out["tiny_f32_64x64"] = pixel_errors(gpu_render(tree, o, d), ref, True)
+    tree.free()
+
+    # NeRF-synthetic-shaped FP16 scene: 200 seeded pixels of each of the 100 views (the oracle
+    # tree and parameters of the baseline's sampler when given)
+    sc, cams = si.config_nerf_synthetic(100)
+    tree = dot.octree_from_scene(sc)
+    if sampler is not None:
+        t, lo, size, s64, h64 = sampler.t, sampler.lo, sampler.size, sampler.s64, sampler.h64
+    else:
+        t = oracle.scene_tree(sc)
+        lo, size = oracle.root_of(sc)
+        s64, h64 = full_params(t, sc)
+    rng = np.random.default_rng(31)
+    oo, dd = zip(*[si.camera_rays(c, rng.choice(c.width * c.height, 200, replace=False)) for c in cams])
+    o, d = np.concatenate(oo), np.concatenate(dd)
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, sc.sh_degree, o, d, eps_T=1e-4, threads=threads)
+    out["nerf_synthetic_f16_800"] = pixel_errors(gpu_render(tree, o, d), ref, False)
+
+    # gradients of one 2^16-ray batch through the fused pass
+    o, d = si.ray_batch(cams, BATCH, seed=8123)
+    _, _, _, margin = oracle.render(t, lo, size, s64, h64, sc.sh_degree, o, d, eps_T=1e-4,
+                                    margin=True, threads=threads)
+    keep = margin > 1e-3
+    o, d = np.ascontiguousarray(o[keep]), np.ascontiguousarray(d[keep])
+    R = o.shape[0]
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, sc.sh_degree, o, d, eps_T=1e-4, threads=threads)
+    tgt = np.where(ref > 0.5, ref - 0.45, ref + 0.45).astype(np.float32)
+    L, K = tree.n_leaves, sc.n_coeffs
+    rgb, g = torch.empty(R, 3, device="cuda"), torch.empty(R, 3, device="cuda")
+    gs, gsh = torch.zeros(L, device="cuda"), torch.zeros(L, 3, K, device="cuda")
+    dot.dot.dot_render_forward_backward_mse(
+        tree, dot.rays_buffer(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()), opts,
+        torch.from_numpy(tgt).cuda(), rgb, g, gs, gsh)
+    torch.cuda.synchronize()
+    g64 = g.cpu().numpy().astype(np.float64)
+    rs, rsh, asg, ash = oracle.backward(t, lo, size, s64, h64, sc.sh_degree, o, d, g64, eps_T=1e-4)
+    floor = 1e-5 * np.abs(g64).max()
+    out["nerf_synthetic_f16_grad_b16"] = {
+        "rays": R, "rays_set_aside_near_eps_T": int((~keep).sum()),
+        "pixels": pixel_errors(rgb.cpu().numpy(), ref, False),
+        "dsigma": grad_errors(gs.cpu().numpy(), rs, asg, floor),
+        "dsh": grad_errors(gsh.cpu().numpy(), rsh, ash, floor)}
+    tree.free()
+    del s64, h64, t
+
+    # Tanks&Temples-shaped BF16 scene: 64 seeded pixels of each of the 150 views (the oracle gets
+    # the parameters of the leaves these rays cross)
+    sc, cams = si.config_tanks_temples()
+    tree = dot.octree_from_scene(sc)
+    t = oracle.scene_tree(sc)
+    lo, size = oracle.root_of(sc)
+    rng = np.random.default_rng(32)
+    oo, dd = zip(*[si.camera_rays(c, rng.choice(c.width * c.height, 64, replace=False)) for c in cams])
+    o, d = np.concatenate(oo), np.concatenate(dd)
+    crossed = np.unique(np.concatenate([oracle.segments(t, lo, size, o[i], d[i])[0]
+                                        for i in range(o.shape[0])]))
+    s64, h64 = full_params(t, sc, crossed)
+    ref, _, _ = oracle.render(t, lo, size, s64, h64, sc.sh_degree, o, d, eps_T=1e-4, threads=threads)
+    out["tanks_temples_bf16_1080p"] = pixel_errors(gpu_render(tree, o, d), ref, False)
+    tree.free()
+    return out
+
+
 def oracle_baseline(scene, cams, budget_s: float, threads: int, sampler=None):
     """The oracle timed once on a sample of about budget_s seconds."""
     sm = sampler or OracleSample(scene, cams)
@@ -230,6 +369,52 @@ def oracle_baseline(scene, cams, budget_s: float, threads: int, sampler=None):
     dt = sm.time(o, d, threads)
     return {"value": o.shape[0] / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
             "sample": f"{desc} ({o.shape[0]} rays, FP64 forward render, {dt:.1f} s)"}
+
+
+def measure_l2_read(local: int):
+    """L2 read bandwidth for the two-level roofline: the library's L2-only streaming kernel over
+    device buffers of several sizes (the resident ones are served by L2), CUDA events around a
+    call of many passes, SM clocks sampled meanwhile.  Also one buffer far larger than L2 as a
+    check against the measured HBM figure."""
+    import torch
+
+    from paper_2307_15333_gb300 import dot as d
+    stream = torch.cuda.current_stream()
+    sizes_mb = (8, 16, 32, 48, 64, 96)
+    out = {"kernel": "dot_probe_l2_read (ld.global.cg 16-byte loads, whole waves)", "by_size": {}}
+    clocks = Clocks(local)
+    for mb in sizes_mb + (4096,):
+        buf = torch.ones(mb << 20, dtype=torch.uint8, device="cuda")
+        passes = max(2, (2048 if mb < 4096 else 8) * 16 // mb)
+        d.dot_probe_l2_read(buf, 2)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d.dot_probe_l2_read(buf, passes)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out["by_size"][f"{mb}MB"] = (mb << 20) * passes / (best / 1e3) / 1e9
+        del buf
+    out["clocks"] = clocks.stop()
+    resident = [out["by_size"][f"{mb}MB"] for mb in sizes_mb]
+    out["l2_read_gbs"] = max(resident)
+    out["hbm_read_gbs_same_kernel"] = out["by_size"]["4096MB"]
+    return out
+
+
+def two_level(compulsory_bytes, sample_bytes, t_meas_s, hbm_gbs, l2_gbs):
+    """Survey's roofline: t_roof = max(compulsory / HBM bandwidth, sample / L2 bandwidth)."""
+    t_hbm = compulsory_bytes / (hbm_gbs * 1e9)
+    t_l2 = sample_bytes / (l2_gbs * 1e9)
+    t_roof = max(t_hbm, t_l2)
+    return {"compulsory_bytes": compulsory_bytes, "sample_bytes": sample_bytes,
+            "t_hbm_ms": t_hbm * 1e3, "t_l2_ms": t_l2 * 1e3, "t_roof_ms": t_roof * 1e3,
+            "t_meas_ms": t_meas_s * 1e3, "frac": t_roof / t_meas_s,
+            "bound": "l2" if t_l2 >= t_hbm else "hbm"}
 
 
 def measure_serving(args, refined_tree):
@@ -723,6 +908,14 @@ def run_dot(args):
     bst = sum_stats(tree, batches, opts)                  # the nb batches (counting pass)
     b_pair = (alg_bytes_of(bst, bst["rays"], bs, K) + alg_bytes_bwd(bst, bst["rays"], bs, K)) / nb
     b_fused = alg_bytes_fused(bst, bst["rays"], bs, K) / nb
+    # distinct occupied leaves one batch touches (max-weight signal passes, not timed)
+    u_occ_b = []
+    for r in batches:
+        tb = torch.zeros(L, dtype=torch.float32, device="cuda")
+        dot.dot_accumulate_signal(tree, r, opts, dot.dot.DOT_SIGNAL_MAX_WEIGHT, tb)
+        u_occ_b.append(int(torch.count_nonzero(tb)))
+        del tb
+    u_occ_b16 = statistics.mean(u_occ_b)
     fwd_bwd = {"value": BATCH * pairs * ws / (fb_ms / 1e3) / 1e6, "unit": "Mrays/s",
                "batch_rays": BATCH, "pairs": pairs, "ms_per_pair": fb_ms / pairs,
                "grad": "fixed synthetic dL/dC; FP32 gradients accumulate across pairs",
@@ -855,11 +1048,25 @@ def run_dot(args):
                 "+ 12 B per ray",
         "t_at_peak_ms": compulsory / (hbm * 1e9) * 1e3, "t_meas_ms": mean_launch_s * 1e3}
 
-    cpu = None
+    # the survey's two-level roofline with a measured L2 read bandwidth
+    if rank == 0:
+        l2 = measure_l2_read(local)
+        comp_fused = u_occ_b16 * (P + 2 * grad_bytes_per_occupied(K)) + BATCH * 36
+        roofline["two_level"] = {
+            "l2": l2,
+            "forward": two_level(compulsory, alg_bytes, mean_launch_s, hbm, l2["l2_read_gbs"]),
+            "fused_pass_b16": two_level(comp_fused, b_fused, fu_ms / pairs / 1e3, hbm,
+                                        l2["l2_read_gbs"]),
+            "fused_compulsory": "distinct occupied leaves of the batch x (payload + FP32 gradient "
+                                "read and write) + 36 B per ray"}
+
+    cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sampler = OracleSample(scene, cams)
         cpu = oracle_baseline(scene, cams, args.cpu_seconds, os.cpu_count() or 1, sampler)
         cpu["single_thread"] = oracle_baseline(scene, cams, 2.0, 1, sampler)
+        parity = parity_report(os.cpu_count() or 1, sampler if len(cams) == 100 else None)
+        del sampler
 
     line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -873,7 +1080,7 @@ def run_dot(args):
                                                             L * 24 / 1e6),
                        "eps_T": 1e-4, "parallelism": f"replicas{ws}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "fwd_bwd": fwd_bwd, "refine": refine, "train": train_res,
+            "cpu_baseline": cpu, "parity": parity, "fwd_bwd": fwd_bwd, "refine": refine, "train": train_res,
             "train_config3": train3_res,
             "tanks_temples": tt_res, "compressed": comp_res, "serve": serve_res,
             "wall_s_timed": t_wall}

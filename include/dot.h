@@ -539,6 +539,18 @@ int dot_tree_canonicalize(dot_tree *tree, int32_t *leaf_perm, const dot_leaf_arr
 int dot_render_stats(const dot_tree *tree, const dot_rays *rays, const dot_render_opts *opts,
                      int64_t out[4], void *stream);
 
+/*
+ * dot_probe_l2_read -- a measurement helper with no counterpart in the paper: streams `bytes`
+ * of the device buffer `buf` `passes` times with 16-byte loads cached in L2 only, one grid of
+ * whole waves, asynchronous on `stream`.  Timed by the caller (events around the call) on a
+ * buffer that fits in L2, it gives the L2 read bandwidth that the two-level roofline of the
+ * march kernels divides their per-segment bytes by.  buf: device, 16-byte aligned, bytes a
+ * multiple of 16 and > 0; passes >= 1; sink: device uint64 or NULL (written only if the folded
+ * data hits an impossible key, i.e. never in practice).  DOT_ERR_INVALID_ARG otherwise.
+ */
+int dot_probe_l2_read(const void *buf, int64_t bytes, int32_t passes, unsigned long long *sink,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ OUT = os.path.join(HERE, "libdot.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "build.cu", "ropes.cu", "scan.cu", "select.cu", "refine.cu", "render_fwd.cu",
            "render_bwd.cu", "render_signal.cu", "select_noalloc.cu", "render_slots.cu", "train.cu",
-           "compress.cu", "canon.cu", "render_fwd_comp.cu", "render_fwdbwd.cu"]
+           "compress.cu", "canon.cu", "render_fwd_comp.cu", "render_fwdbwd.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

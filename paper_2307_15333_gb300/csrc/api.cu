@@ -648,6 +648,8 @@ extern "C" int dot_select_masks_noalloc(const dot_tree *t, const float *signal,
 }
 
 namespace dot {
+cudaError_t launch_l2_read(const void *buf, int64_t bytes, int32_t passes,
+                           unsigned long long *sink, cudaStream_t s);
 cudaError_t launch_render_slots(int storage, int deg, bool exact, const TreeView *views,
                                 int n_trees, const void *table, int32_t max_slots,
                                 const RenderParams &rp, unsigned long long *counter,
@@ -1118,5 +1120,14 @@ extern "C" int dot_render_views_host(const dot_tree *t, const dot_camera *camera
     API_CK(cudaStreamSynchronize(pipe.copy), where);
     if (pipe.own_render1) API_CK(cudaStreamSynchronize(pipe.render[1]), where);
     API_CK(cudaStreamSynchronize(pipe.render[0]), where);
+    return DOT_OK;
+}
+
+extern "C" int dot_probe_l2_read(const void *buf, int64_t bytes, int32_t passes,
+                                 unsigned long long *sink, void *stream) {
+    if (!buf || bytes <= 0 || bytes % 16 != 0 || (reinterpret_cast<uintptr_t>(buf) & 15) != 0)
+        return fail(DOT_ERR_INVALID_ARG, "buf must be 16-byte aligned and bytes a positive multiple of 16");
+    if (passes < 1) return fail(DOT_ERR_INVALID_ARG, "passes must be >= 1");
+    API_CK(dot::launch_l2_read(buf, bytes, passes, sink, S(stream)), "dot_probe_l2_read");
     return DOT_OK;
 }

@@ -42,7 +42,8 @@ ENTRY_POINTS = ("dot_last_error", "dot_version", "dot_octree_build", "dot_tree_f
                 "dot_select_masks_noalloc", "dot_render_slots", "dot_mse_grad",
                 "dot_rmsprop_step", "dot_compress_sh", "dot_tree_canonicalize",
                 "dot_rmsprop_step_sparse", "dot_rmsprop_flush", "dot_render_forward_backward_mse",
-                "dot_camera_order", "dot_render_views_host", "dot_render_views_host_workspace")
+                "dot_camera_order", "dot_render_views_host", "dot_render_views_host_workspace",
+                "dot_probe_l2_read")
 
 _TORCH_OF_STORAGE = {DOT_STORAGE_F32: torch.float32, DOT_STORAGE_F16: torch.float16,
                      DOT_STORAGE_BF16: torch.bfloat16}
@@ -184,6 +185,7 @@ def lib() -> ctypes.CDLL:
         "dot_camera_order": [P, ctypes.c_int32, P],
         "dot_render_views_host": [P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
                                   ctypes.POINTER(dot_render_opts), P, P, P, ctypes.c_int64, P],
+        "dot_probe_l2_read": [P, ctypes.c_int64, ctypes.c_int32, P, P],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -794,3 +796,12 @@ def dot_tree_canonicalize(tree: Octree, leaf_perm: torch.Tensor, aux: Sequence =
 
 def dot_tree_status(tree: Octree, stream=None) -> int:
     return tree.status(stream)
+
+
+def dot_probe_l2_read(buf: torch.Tensor, passes: int, sink: Optional[torch.Tensor] = None,
+                      stream=None):
+    """Streams the device buffer `passes` times with L2-only loads (a bandwidth measurement)."""
+    if not buf.is_cuda:
+        raise ValueError("buf must be a device tensor")
+    nbytes = buf.numel() * buf.element_size()
+    _check(lib().dot_probe_l2_read(_ptr(buf), nbytes, int(passes), _ptr(sink), _stream(stream)))

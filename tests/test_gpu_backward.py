@@ -5,7 +5,7 @@ import torch
 
 import oracle
 import seeded_inputs as si
-from helpers import assert_sums_close, oracle_side
+from helpers import assert_sums_close, assert_sums_close_grazing, oracle_side
 
 pytestmark = pytest.mark.gpu
 
@@ -221,10 +221,13 @@ def test_fused_training_pass_overflow_rays_march_again():
 def test_full_size_fused_training_pass_matches_oracle():
     """The bench's training configuration at full size: a 2^16-ray batch from the 100 views of the
     NeRF-synthetic-shaped scene (2.9 M leaves, FP16, SH degree 3) through the fused pass, against
-    the oracle's render, MSE gradient and backward of the same rays.  The targets sit 0.45 away
-    from the oracle's colours, so the GPU's dL/dC (taken at its own colours, within 2e-3 of the
-    oracle's) is within 0.5% of the oracle's; gradients are compared at 1e-2 of their summed
-    magnitudes."""
+    the oracle's render, MSE gradient and backward of the same rays.  The fused pass takes dL/dC
+    at its own colours; that dL/dC is checked against the oracle's (within the pixel tolerance
+    times 2 / 3R) and then handed to the oracle's backward, so the gradients are held to the
+    16-bit rule of every other backward test: 2e-3 of the summed magnitudes, plus a floor of
+    1e-5 in units of the largest |dL/dC| -- with the grazing-ray budget of a large fast-mode
+    batch: at most 0.1% of the leaves with a gradient may exceed it (sliver segments of rays
+    that graze a face), none by more than 1e-3 of the largest |dL/dC|."""
     import paper_2307_15333_gb300 as dot
     scene, cams = si.config_nerf_synthetic(100)
     tree = dot.octree_from_scene(scene)
@@ -249,7 +252,13 @@ def test_full_size_fused_training_pass_matches_oracle():
     assert np.abs(rgb.cpu().numpy() - ref).max() <= 2e-3
     ref_loss, ref_g = oracle.mse(ref, tgt)
     assert float(loss) == pytest.approx(ref_loss, rel=1e-2)
-    rs, rsh, asg, ash = oracle.backward(t, lo, size, s64, h64, 3, o, d, ref_g, eps_T=1e-4)
-    assert_sums_close(gs.cpu().numpy(), rs, asg, 1e-2, "dsigma", 1e-8)
-    assert_sums_close(gsh.cpu().numpy(), rsh, ash, 1e-2, "dsh", 1e-8)
+    g_gpu = g.cpu().numpy().astype(np.float64)
+    assert np.abs(g_gpu - ref_g).max() <= 2 * 2e-3 / (3 * R) * 1.001
+    rs, rsh, asg, ash = oracle.backward(t, lo, size, s64, h64, 3, o, d, g_gpu, eps_T=1e-4)
+    floor = 1e-5 * np.abs(g_gpu).max()
+    assert np.abs(rs).max() > 100 * floor
+    nb_s, nl_s, w_s = assert_sums_close_grazing(gs.cpu().numpy(), rs, asg, 2e-3, "dsigma", floor)
+    nb_h, nl_h, w_h = assert_sums_close_grazing(gsh.cpu().numpy(), rsh, ash, 2e-3, "dsh", floor)
+    print(f"grazing exceptions: dsigma {nb_s}/{nl_s} (worst excess {w_s:.3g} x floor), "
+          f"dsh {nb_h}/{nl_h} (worst excess {w_h:.3g} x floor)")
     tree.free()
