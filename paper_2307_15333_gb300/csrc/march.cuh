@@ -546,12 +546,28 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (nrec <= kRecordSegments) {
 #pragma unroll
             for (int ch = 0; ch < 3; ch++) C[ch] = 0.f;
-            for (int i = 0; i < nrec; i++) {
-                const float4 a = rec[2 * i], b = rec[2 * i + 1];
-                const float col[3] = {b.x, b.y, b.z};
+            // the record is read kScatterAhead entries at a time, all loads issued before the
+            // first of them is used (one record round trip per group, not per segment: 173.6 ->
+            // 165.7 us per 2^16-ray pass; 2 entries 168.3)
+            constexpr int kScatterAhead = 4;
+            for (int i0 = 0; i0 < nrec; i0 += kScatterAhead) {
+                float4 a[kScatterAhead], b[kScatterAhead];
 #pragma unroll
-                for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(a.y, col[ch], C[ch]);
-                scatter(__float_as_int(a.x), a.y, a.z, a.w, col);
+                for (int u = 0; u < kScatterAhead; u++) {
+                    if (i0 + u < nrec) {
+                        a[u] = rec[2 * (i0 + u)];
+                        b[u] = rec[2 * (i0 + u) + 1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kScatterAhead; u++) {
+                    if (i0 + u < nrec) {
+                        const float col[3] = {b[u].x, b[u].y, b[u].z};
+#pragma unroll
+                        for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(a[u].y, col[ch], C[ch]);
+                        scatter(__float_as_int(a[u].x), a[u].y, a[u].z, a[u].w, col);
+                    }
+                }
             }
         } else {
             out.overflow = true;  // the caller re-marches this ray in the backward mode
@@ -666,11 +682,19 @@ march_kernel(TreeView tv, RaySource rs, RenderParams rp, RenderIO io) {
         }
     }
     if constexpr (MODE == kFwdBwd) {
-        if (io.loss_sum) {
+        if (io.loss_sum) {  // block sum of the squared errors, one double atomic per block
+            __shared__ double s_loss[NT / 32];
             float l = valid ? out.loss : 0.f;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
-            if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(io.loss_sum, (double)l * io.inv3R);
+            if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = (double)l * io.inv3R;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double b = 0.0;
+#pragma unroll
+                for (int w = 0; w < NT / 32; w++) b += s_loss[w];
+                if (b != 0.0) atomicAdd(io.loss_sum, b);
+            }
         }
     }
     if constexpr (MODE == kStats) {
