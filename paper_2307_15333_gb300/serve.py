@@ -104,23 +104,30 @@ def slot_groups(trees) -> List[List[int]]:
     return groups
 
 
-def pack_table(reqs: Sequence[Request], pool_base_ptr: int, max_slots: int,
-               tree_index=None) -> np.ndarray:
-    """Byte image of a slot table: header then one 96-byte dot_slot per request.  tree_index
-    maps a request's tree to its index in the launch's tree list (identity if None)."""
+def write_slots(buf: np.ndarray, reqs: Sequence[Request], pool_base_ptr: int, max_slots: int,
+                tree_index=None) -> None:
+    """Writes a slot table in place into the byte buffer `buf` (HEADER_BYTES + SLOT_BYTES *
+    max_slots): the header, then one 96-byte dot_slot per request.  Slots past the last request
+    keep whatever they held: the kernel reads n_slots of them.  tree_index maps a request's tree
+    to its index in the launch's tree list (identity if None)."""
     assert len(reqs) <= max_slots
-    buf = np.zeros(HEADER_BYTES + SLOT_BYTES * max_slots, dtype=np.uint8)
     begin = 0
     for i, r in enumerate(reqs):
         rec = buf[HEADER_BYTES + SLOT_BYTES * i: HEADER_BYTES + SLOT_BYTES * (i + 1)]
         rec[0:72] = np.ascontiguousarray(r.camera, dtype=np.float32).view(np.uint8)
         t = r.tree if tree_index is None else tree_index[r.tree]
-        rec[72:76] = np.array([t], np.int32).view(np.uint8)
-        rec[80:88] = np.array([begin], np.int64).view(np.uint8)
-        rec[88:96] = np.array([pool_base_ptr + 4 * r.offset], np.uint64).view(np.uint8)
+        rec[72:80] = np.array([t, 0], np.int32).view(np.uint8)
+        rec[80:96] = np.array([begin, pool_base_ptr + 4 * r.offset], np.uint64).view(np.uint8)
         begin += r.tiles
-    buf[0:4] = np.array([len(reqs)], np.int32).view(np.uint8)
-    buf[8:16] = np.array([begin], np.int64).view(np.uint8)
+    buf[0:16] = np.array([len(reqs), 0, begin & 0xFFFFFFFF, begin >> 32], np.uint32).view(np.uint8)
+
+
+def pack_table(reqs: Sequence[Request], pool_base_ptr: int, max_slots: int,
+               tree_index=None) -> np.ndarray:
+    """Byte image of a slot table: header then one 96-byte dot_slot per request (zero-filled
+    after the last request)."""
+    buf = np.zeros(HEADER_BYTES + SLOT_BYTES * max_slots, dtype=np.uint8)
+    write_slots(buf, reqs, pool_base_ptr, max_slots, tree_index)
     return buf
 
 
@@ -162,24 +169,29 @@ def _no_gc_pauses():
 
 class _Table:
     """One slot table per tree group, back to back in one pinned host buffer and one device
-    buffer (one copy per replay), a work counter per group, and the streams the group launches
-    fork onto."""
+    buffer, a work counter per group, the streams the group launches fork onto, and one CUDA graph
+    per set of groups a batch can hold (a batch replays the graph of the groups it uses: no launch
+    for an empty group, and only the used sub-tables are copied)."""
 
     def __init__(self, torch, max_slots, n_groups):
         self.table_bytes = HEADER_BYTES + SLOT_BYTES * max_slots
         nbytes = self.table_bytes * n_groups
         self.host = torch.zeros(nbytes, dtype=torch.uint8, pin_memory=True)
+        self.host_np = self.host.numpy()
         self.dev = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
         self.counter = torch.zeros(n_groups, dtype=torch.int64, device="cuda")
         self.stream = torch.cuda.Stream()
         self.forks = [torch.cuda.Stream() for _ in range(n_groups - 1)]
-        self.graph = None
+        self.graphs = {}                        # bit mask of the groups used -> CUDA graph
         self.event = torch.cuda.Event()
         self.reqs: List[Request] = []
 
 
 class BatchedServer:
-    def __init__(self, trees, opts, pool_floats: int, max_slots: int = 256, n_tables: int = 2):
+    # up to this many tree groups, a graph per non-empty set of groups; beyond, one graph of all
+    MAX_SUBSET_GROUPS = 4
+
+    def __init__(self, trees, opts, pool_floats: int, max_slots: int = 64, n_tables: int = 2):
         import torch
 
         from . import dot
@@ -190,15 +202,20 @@ class BatchedServer:
         for g, members in enumerate(self.groups):
             for j, t in enumerate(members):
                 self.local[t] = (g, j)
+        self.index = [{t: self.local[t][1] for t in m} for m in self.groups]
         self.handles = [(ctypes.c_void_p * len(m))(*[self.trees[t].handle.value for t in m])
                         for m in self.groups]
         self.opts = opts
         self.max_slots = max_slots
         self.pool_t = torch.empty(int(pool_floats), dtype=torch.float32, device="cuda")
         self.pool = OutputPool(pool_floats)
-        self.tables = [_Table(torch, max_slots, len(self.groups)) for _ in range(n_tables)]
+        G = len(self.groups)
+        full = (1 << G) - 1
+        self.masks = list(range(1, full + 1)) if G <= self.MAX_SUBSET_GROUPS else [full]
+        self.tables = [_Table(torch, max_slots, G) for _ in range(n_tables)]
         for tb in self.tables:
-            self._capture(tb)
+            for m in self.masks:
+                self._capture(tb, m)
 
     def _launch(self, tb, g):
         torch = self.torch
@@ -210,40 +227,48 @@ class BatchedServer:
         if rc != 0:
             raise self.dot.DotError(rc, self.dot.dot_last_error())
 
-    def _record(self, tb):
-        """The work of one replay: the table copy, then one slot launch per group -- the first on
-        the table's stream, the others on forked streams that join it again."""
+    def _record(self, tb, mask):
+        """The work of one replay for the groups in `mask`: their sub-tables copied, then one slot
+        launch per group -- the first on the table's stream, the others on forked streams that
+        join it again."""
         torch = self.torch
-        tb.dev.copy_(tb.host, non_blocking=True)
-        for g, fork in enumerate(tb.forks, start=1):
+        used = [g for g in range(len(self.groups)) if mask >> g & 1]
+        for g in used:
+            a, b = g * tb.table_bytes, (g + 1) * tb.table_bytes
+            tb.dev[a:b].copy_(tb.host[a:b], non_blocking=True)
+        for g, fork in zip(used[1:], tb.forks):
             fork.wait_stream(tb.stream)
             with torch.cuda.stream(fork):
                 self._launch(tb, g)
-        self._launch(tb, 0)
-        for fork in tb.forks:
+        self._launch(tb, used[0])
+        for _, fork in zip(used[1:], tb.forks):
             tb.stream.wait_stream(fork)
 
-    def _capture(self, tb):
+    def _capture(self, tb, mask):
         torch = self.torch
         with torch.cuda.stream(tb.stream):          # one eager run before capture
-            self._record(tb)
+            self._record(tb, mask)
         torch.cuda.synchronize()
-        tb.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(tb.graph, stream=tb.stream):
-            self._record(tb)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=tb.stream):
+            self._record(tb, mask)
         torch.cuda.synchronize()
+        tb.graphs[mask] = graph
 
     def submit(self, reqs: List[Request], tb: _Table):
-        host = tb.host.numpy()
         base = self.pool_t.data_ptr()
-        for g, members in enumerate(self.groups):
-            mine = [r for r in reqs if self.local[r.tree][0] == g]
-            index = {t: self.local[t][1] for t in members}
-            host[g * tb.table_bytes:(g + 1) * tb.table_bytes] = pack_table(
-                mine, base, self.max_slots, index)
+        by_group = [[] for _ in self.groups]
+        for r in reqs:
+            by_group[self.local[r.tree][0]].append(r)
+        mask = 0
+        for g, mine in enumerate(by_group):
+            if mine or len(self.masks) == 1:
+                mask |= 1 << g
+                write_slots(tb.host_np[g * tb.table_bytes:(g + 1) * tb.table_bytes], mine, base,
+                            self.max_slots, self.index[g])
         tb.reqs = reqs
         with self.torch.cuda.stream(tb.stream):
-            tb.graph.replay()
+            tb.graphs[mask].replay()
             tb.event.record(tb.stream)
 
     def run(self, trace: Sequence[Request], clock=time.perf_counter):
