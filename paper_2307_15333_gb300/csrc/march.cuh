@@ -80,6 +80,53 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// L2 eviction policies of small launches: the traversal data (ropes, densities, child rows) is
+// loaded evict-last and the SH rows evict-first, so that a batch's stream of rows does not push
+// the next steps' ropes and densities out of L2 (2^16-ray batches: forward 122.8 -> 116.5 us,
+// fused pass 164.3 -> 156.6 us; the full-size launches, whose L2 holds other rays' leaves, are
+// slower with it, 8.71 -> 9.25 ms, and keep plain loads)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int32_t ld_hint(const int32_t *a, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t *a, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(a), "l"(pol));
+    return v;
+}
+template <typename S> __device__ __forceinline__ float ld_hint_storage(const S *a, uint64_t pol) {
+    if constexpr (sizeof(S) == 2) {
+        unsigned short h;
+        asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(h) : "l"(a), "l"(pol));
+        if constexpr (std::is_same<S, __half>::value) return __half2float(__ushort_as_half(h));
+        else return __bfloat162float(__ushort_as_bfloat16(h));
+    } else {
+        float f;
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(f) : "l"(a), "l"(pol));
+        return f;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // SH rows: [3][K] coefficients in the storage type, padded to 16-byte vectors
 // ---------------------------------------------------------------------------------------------
 template <typename S, int K> struct Row {
@@ -88,15 +135,17 @@ template <typename S, int K> struct Row {
 };
 
 // z[ch] = sum_k row[ch][k] Y_k in FP32, one 16-byte vector of the row at a time (each channel's
-// terms summed in k order)
-template <typename S, int K>
-__device__ __forceinline__ void leaf_z(const S *row, const float *Y, float z[3]) {
+// terms summed in k order); HINT: the row is loaded with L2 policy `pol`
+template <typename S, int K, bool HINT = false>
+__device__ __forceinline__ void leaf_z(const S *row, const float *Y, float z[3], uint64_t pol = 0) {
     constexpr int E = 16 / (int)sizeof(S);
     const uint4 *p = reinterpret_cast<const uint4 *>(row);
     float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < Row<S, K>::kVec; i++) {
-        const uint4 v = __ldg(p + i);
+        uint4 v;
+        if constexpr (HINT) v = ld_hint(p + i, pol);
+        else v = __ldg(p + i);
         const S *e = reinterpret_cast<const S *>(&v);
 #pragma unroll
         for (int j = 0; j < E; j++) {
@@ -293,6 +342,12 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
 
     const S *sigma = reinterpret_cast<const S *>(tv.sigma);
     const S *shp = reinterpret_cast<const S *>(tv.sh);
+    // small launches (DEFER): L2 policies of the traversal loads and of the SH rows
+    uint64_t pol_keep = 0, pol_stream = 0;
+    if constexpr (DEFER) {
+        pol_keep = l2_policy_last();
+        pol_stream = l2_policy_first();
+    }
 
     // descend from (node, level) to the leaf holding gc
     auto descend = [&](int32_t node, int level, int32_t &leaf_out, int &level_out) -> bool {
@@ -301,7 +356,8 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         while (true) {
             const int sh = kGridBits - 1 - level;
             const int j = ((g0 >> sh) & 4) | ((g1 >> sh) & 2) | ((g2 >> sh) & 1);
-            c = __ldg(tv.child + (int64_t)node * 8 + j);
+            if constexpr (DEFER) c = ld_hint(tv.child + (int64_t)node * 8 + j, pol_keep);
+            else c = __ldg(tv.child + (int64_t)node * 8 + j);
             ++level;
             if constexpr (MODE == kStats) out.st[3] += 1;
             if (c < 0 || level >= tv.max_level) break;
@@ -358,7 +414,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     auto shade = [&](int32_t lf, int64_t row, float w, float Tn, float delta) {
         if constexpr (SHADE) {
             float z[3], col[3];
-            leaf_z<S, K>(shp + row * tv.row_stride, Y, z);
+            leaf_z<S, K, DEFER>(shp + row * tv.row_stride, Y, z, pol_stream);
 #pragma unroll
             for (int ch = 0; ch < 3; ch++)
                 col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
@@ -398,11 +454,14 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         float sv;
         int64_t row;  // SH row of the leaf: its own, or its palette entry
         if constexpr (COMP) {
-            const uint32_t w = __ldg(tv.rec + leaf);
+            uint32_t w;
+            if constexpr (DEFER) w = ld_hint(tv.rec + leaf, pol_keep);
+            else w = __ldg(tv.rec + leaf);
             sv = Storage<S>::from_bits16(w);
             row = w >> 16;
         } else {
-            sv = Storage<S>::load(sigma + leaf);
+            if constexpr (DEFER) sv = ld_hint_storage<S>(sigma + leaf, pol_keep);
+            else sv = Storage<S>::load(sigma + leaf);
             row = leaf;
         }
         const int cs = 1 << (kGridBits - level);
@@ -472,7 +531,9 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if (!outside) {
             bool found;
             if (crossed == 1) {  // across one face: its rope
-                const int32_t rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
+                int32_t rp;
+                if constexpr (DEFER) rp = ld_hint(tv.rope + (int64_t)leaf * 6 + face, pol_keep);
+                else rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
                 if constexpr (MODE == kStats) out.st[3] += 1;
                 if (rp >= 0) {  // the node at this leaf's level: descend into the finer neighbour
                     found = rp < tv.n_nodes && descend(rp, level, next_leaf, next_level);
