@@ -4,15 +4,22 @@
 // rendered segment reads 4 bytes per leaf plus a palette row that stays resident in L2
 // (2^16 rows x 96 bytes = 6.3 MB at SH degree 3).
 //
-// The quantiser is an offline step and runs on the host: copy the rows out, median cut, write the
-// palette and the records back.  Median cut rules: each of the bits rounds splits every box of two
-// or more vectors at the median of its longest axis (largest max - min, computed in double; ties
-// to the lowest axis), the members ordered by (value on that axis, leaf id), floor(m/2) of them
-// to child 2b and the rest to child 2b + 1; a palette row is the mean of its box (zeros if empty),
-// rounded to the storage type.
+// Median cut rules: each of the bits rounds splits every box of two or more vectors at the median
+// of its longest axis (largest max - min, computed in double; ties to the lowest axis), the
+// members ordered by (value on that axis, leaf id), floor(m/2) of them to child 2b and the rest
+// to child 2b + 1 (a box of fewer than two keeps its members in child 2b); a palette row is the
+// mean of its box (zeros if empty), rounded to the storage type.
+//
+// On the GPU every leaf carries its box number; no member lists are kept.  A round:
+//   1. per box and axis, the min and max of the members (order-preserving 32-bit keys, atomics
+//      aggregated over the lanes of a warp that share a box), and the member count;
+//   2. per box, the longest axis;
+//   3. per box, the member of rank floor(m/2) in (value, id) order: a radix select over the
+//      64-bit keys (value key << 32 | leaf id), unique per leaf, in 8 histogram passes of 8 bits;
+//   4. every leaf moves to child 2b, or 2b + 1 if its key is at or above that member's.
+// The palette is then the per-box mean of FP64 sums.
 #include <algorithm>
-#include <thread>
-#include <vector>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "tree.cuh"
@@ -21,99 +28,266 @@ namespace dot {
 
 namespace {
 
-float bits_to_float(uint16_t b, int storage) {
-    if (storage == DOT_STORAGE_F16) {
-        __half_raw r;
-        r.x = b;
-        return __half2float(__half(r));
-    }
-    __nv_bfloat16_raw r;
-    r.x = b;
-    return __bfloat162float(__nv_bfloat16(r));
+constexpr int kMcThreads = 256;
+
+// order-preserving key of a float (a smaller float has a smaller key)
+__device__ __forceinline__ unsigned mc_key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float mc_val(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-uint16_t double_to_bits(double v, int storage) {
-    if (storage == DOT_STORAGE_F16) {
-        __half_raw r = __double2half(v);
-        return r.x;
-    }
-    __nv_bfloat16_raw r = __double2bfloat16(v);
-    return r.x;
+template <typename S>
+__device__ __forceinline__ float mc_coef(const S *rows, int64_t v, int stride, int d) {
+    return Storage<S>::to_f32(rows[v * stride + d]);
 }
 
-template <typename F>
-void parallel_for(int64_t n, F &&f) {
-    const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
-    const int64_t nt = std::min<int64_t>(hw, n);
-    if (nt <= 1) {
-        for (int64_t i = 0; i < n; i++) f(i);
+struct McBox {
+    int32_t count;
+    int32_t axis;              // -1: fewer than two members, not split
+    unsigned long long prefix; // radix select: key bits fixed so far
+    unsigned long long mask;
+    long long krem;            // 1-based rank still to find among keys matching prefix / mask
+};
+
+__global__ void mc_clear_kernel(unsigned *lo, unsigned *hi, McBox *box, int64_t n_boxes, int dim) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_boxes * dim) {
+        lo[i] = 0xffffffffu;
+        hi[i] = 0u;
+    }
+    if (i < n_boxes) box[i].count = 0;
+}
+
+// min / max per (box, axis) and the member counts; lanes of a warp with the same box combine
+// their values before the atomic
+template <typename S>
+__global__ void __launch_bounds__(kMcThreads)
+mc_minmax_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
+                 const int32_t *__restrict__ box_of, unsigned *lo, unsigned *hi, McBox *box) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = v < L;
+    const int b = ok ? box_of[v] : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    const bool leader = (threadIdx.x & 31) == (__ffs(grp) - 1);
+    if (ok && leader) atomicAdd(&box[b].count, __popc(grp));
+    for (int d = 0; d < dim; d++) {
+        const unsigned k = ok ? mc_key(mc_coef(rows, v, stride, d)) : 0u;
+        const unsigned kmin = __reduce_min_sync(grp, k), kmax = __reduce_max_sync(grp, k);
+        if (ok && leader) {
+            atomicMin(lo + (int64_t)b * dim + d, kmin);
+            atomicMax(hi + (int64_t)b * dim + d, kmax);
+        }
+    }
+}
+
+// longest axis of every box; the radix select starts at rank floor(m/2) + 1 (1-based)
+__global__ void mc_axis_kernel(const unsigned *lo, const unsigned *hi, McBox *box, int64_t n_boxes,
+                               int dim) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    McBox &x = box[b];
+    x.prefix = 0ull;
+    x.mask = 0ull;
+    if (x.count < 2) {
+        x.axis = -1;
         return;
     }
-    std::vector<std::thread> th;
-    for (int64_t t = 0; t < nt; t++)
-        th.emplace_back([&, t] {
-            for (int64_t i = t; i < n; i += nt) f(i);
-        });
-    for (auto &x : th) x.join();
+    int axis = 0;
+    double best = -1.0;
+    for (int d = 0; d < dim; d++) {
+        const double range = (double)mc_val(hi[b * dim + d]) - (double)mc_val(lo[b * dim + d]);
+        if (range > best) {
+            best = range;
+            axis = d;
+        }
+    }
+    x.axis = axis;
+    x.krem = x.count / 2 + 1;
 }
 
-// x: n vectors of dim floats (exact copies of 16-bit values); index[n] and palette[P][dim]
-void median_cut(int64_t n, int dim, const float *x, int bits, std::vector<int32_t> &index,
-                std::vector<double> &palette) {
-    const int64_t P = int64_t(1) << bits;
-    std::vector<int64_t> order(n);
-    for (int64_t i = 0; i < n; i++) order[i] = i;
-    std::vector<int64_t> start{0, n}, next;
-    for (int r = 0; r < bits; r++) {
-        const int64_t boxes = (int64_t)start.size() - 1;
-        next.assign(2 * boxes + 1, 0);
-        parallel_for(boxes, [&](int64_t b) {
-            const int64_t s = start[b], e = start[b + 1], m = e - s;
-            next[2 * b] = s;
-            if (m < 2) {
-                next[2 * b + 1] = e;
-                return;
-            }
-            std::vector<float> lo(x + order[s] * dim, x + order[s] * dim + dim), hi = lo;
-            for (int64_t k = s + 1; k < e; k++) {
-                const float *v = x + order[k] * dim;
-                for (int d = 0; d < dim; d++) {
-                    lo[d] = std::min(lo[d], v[d]);
-                    hi[d] = std::max(hi[d], v[d]);
-                }
-            }
-            int axis = 0;
-            double best = -1.0;
-            for (int d = 0; d < dim; d++) {
-                const double range = (double)hi[d] - (double)lo[d];
-                if (range > best) {
-                    best = range;
-                    axis = d;
-                }
-            }
-            std::nth_element(order.begin() + s, order.begin() + s + m / 2, order.begin() + e,
-                             [&](int64_t i, int64_t j) {
-                                 const float u = x[i * dim + axis], w = x[j * dim + axis];
-                                 return u < w || (u == w && i < j);
-                             });
-            next[2 * b + 1] = s + m / 2;
-        });
-        next[2 * boxes] = n;
-        start.swap(next);
+template <typename S>
+__device__ __forceinline__ unsigned long long mc_select_key(const S *rows, int stride, int64_t v,
+                                                            int axis) {
+    return ((unsigned long long)mc_key(mc_coef(rows, v, stride, axis)) << 32) | (unsigned long long)v;
+}
+
+// one radix-select pass: per box, the histogram of the digit at `shift` of the keys that match the
+// box's prefix so far
+template <typename S>
+__global__ void __launch_bounds__(kMcThreads)
+mc_hist_kernel(const S *__restrict__ rows, int stride, int64_t L, const int32_t *__restrict__ box_of,
+               const McBox *__restrict__ box, int shift, unsigned *hist) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= L) return;
+    const int b = box_of[v];
+    const McBox x = box[b];
+    if (x.axis < 0) return;
+    const unsigned long long k = mc_select_key(rows, stride, v, x.axis);
+    if ((k & x.mask) != x.prefix) return;
+    atomicAdd(hist + (int64_t)b * 256 + ((k >> shift) & 255u), 1u);
+}
+
+// one warp per box: the digit holding rank krem; the histogram is cleared for the next pass
+__global__ void mc_pick_kernel(unsigned *hist, McBox *box, int64_t n_boxes, int shift) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_boxes) return;
+    McBox &x = box[b];
+    unsigned *h = hist + b * 256;
+    if (x.axis < 0) return;  // never histogrammed
+    unsigned c[8];
+    long long sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        c[i] = h[lane * 8 + i];
+        sum += c[i];
     }
-    index.assign(n, 0);
-    palette.assign(P * dim, 0.0);
-    parallel_for(P, [&](int64_t b) {
-        const int64_t s = start[b], e = start[b + 1];
-        double *row = palette.data() + b * dim;
-        for (int64_t k = s; k < e; k++) {
-            index[order[k]] = (int32_t)b;
-            const float *v = x + order[k] * dim;
-            for (int d = 0; d < dim; d++) row[d] += (double)v[d];
+    long long incl = sum;  // inclusive scan of the lanes' sums
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const long long krem = x.krem;
+    long long base = incl - sum;
+    int digit = -1;
+    long long below = 0;
+    if (base < krem && krem <= incl) {
+        for (int i = 0; i < 8; i++) {
+            if (base + c[i] >= krem) {
+                digit = lane * 8 + i;
+                below = base;
+                break;
+            }
+            base += c[i];
         }
-        if (e > s)
-            for (int d = 0; d < dim; d++) row[d] /= (double)(e - s);
-    });
+    }
+    const unsigned found = __ballot_sync(0xffffffffu, digit >= 0);
+    const int src = __ffs(found) - 1;
+    const int d = __shfl_sync(0xffffffffu, digit, src < 0 ? 0 : src);
+    const long long bl = __shfl_sync(0xffffffffu, below, src < 0 ? 0 : src);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; i++) h[lane * 8 + i] = 0u;
+    if (lane == 0 && src >= 0) {
+        x.prefix |= (unsigned long long)d << shift;
+        x.mask |= 255ull << shift;
+        x.krem = krem - bl;
+    }
+}
+
+// split: below the selected member's key -> child 2b, at or above -> child 2b + 1
+template <typename S>
+__global__ void mc_assign_kernel(const S *__restrict__ rows, int stride, int64_t L,
+                                 int32_t *box_of, const McBox *__restrict__ box) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= L) return;
+    const int b = box_of[v];
+    const McBox x = box[b];
+    int child = 2 * b;
+    if (x.axis >= 0 && mc_select_key(rows, stride, v, x.axis) >= x.prefix) child += 1;
+    box_of[v] = child;
+}
+
+__global__ void mc_init_kernel(int32_t *box_of, int64_t L) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < L) box_of[v] = 0;
+}
+
+// FP64 sums of every final box's members, and their counts
+template <typename S>
+__global__ void __launch_bounds__(kMcThreads)
+mc_sum_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
+              const int32_t *__restrict__ box_of, double *sum, int32_t *count) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= L) return;
+    const int b = box_of[v];
+    atomicAdd(count + b, 1);
+    for (int d = 0; d < dim; d++)
+        atomicAdd(sum + (int64_t)b * dim + d, (double)mc_coef(rows, v, stride, d));
+}
+
+template <typename S>
+__global__ void mc_palette_kernel(const double *sum, const int32_t *count, int64_t P, int dim,
+                                  int stride, S *palette) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * stride) return;
+    const int64_t b = i / stride;
+    const int d = (int)(i - b * stride);
+    double m = 0.0;
+    if (d < dim && count[b] > 0) m = sum[b * dim + d] / (double)count[b];
+    if constexpr (std::is_same<S, __half>::value) palette[i] = __double2half(m);
+    else palette[i] = __double2bfloat16(m);
+}
+
+template <typename S>
+__global__ void mc_record_kernel(const S *sigma, const int32_t *box_of, int64_t L, uint32_t *rec) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= L) return;
+    unsigned short bits;
+    if constexpr (std::is_same<S, __half>::value) bits = __half_as_ushort(sigma[v]);
+    else bits = __bfloat16_as_ushort(sigma[v]);
+    rec[v] = (uint32_t)bits | ((uint32_t)box_of[v] << 16);
+}
+
+#define MC_CK(x)                             \
+    do {                                     \
+        cudaError_t e_ = (x);                \
+        if (e_ != cudaSuccess) return e_;    \
+    } while (0)
+
+inline unsigned blocks_of(int64_t n, int t = kMcThreads) { return (unsigned)((n + t - 1) / t); }
+
+template <typename S>
+cudaError_t median_cut(const S *rows, const S *sigma, int64_t L, int dim, int stride, int bits,
+                       S *palette, uint32_t *rec, char *scratch, cudaStream_t s) {
+    const int64_t P = int64_t(1) << bits, half = P / 2;
+    // scratch layout (256-byte aligned pieces)
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    int32_t *box_of = reinterpret_cast<int32_t *>(scratch);
+    size_t off = up((size_t)L * 4);
+    unsigned *lo = reinterpret_cast<unsigned *>(scratch + off);
+    off += up((size_t)half * dim * 4);
+    unsigned *hi = reinterpret_cast<unsigned *>(scratch + off);
+    off += up((size_t)half * dim * 4);
+    McBox *box = reinterpret_cast<McBox *>(scratch + off);
+    off += up((size_t)half * sizeof(McBox));
+    unsigned *hist = reinterpret_cast<unsigned *>(scratch + off);
+    off += up((size_t)half * 256 * 4);
+    double *sum = reinterpret_cast<double *>(scratch + off);
+    off += up((size_t)P * dim * 8);
+    int32_t *count = reinterpret_cast<int32_t *>(scratch + off);
+
+    if (L == 0) return cudaMemsetAsync(palette, 0, (size_t)P * stride * sizeof(S), s);
+    MC_CK(cudaMemsetAsync(hist, 0, (size_t)half * 256 * 4, s));
+    mc_init_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(box_of, L);
+    for (int r = 0; r < bits; r++) {
+        const int64_t nb = int64_t(1) << r;
+        mc_clear_kernel<<<blocks_of(nb * dim), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
+        mc_minmax_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo, hi, box);
+        mc_axis_kernel<<<blocks_of(nb), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            mc_hist_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, L, box_of, box, shift, hist);
+            mc_pick_kernel<<<blocks_of(nb * 32), kMcThreads, 0, s>>>(hist, box, nb, shift);
+        }
+        mc_assign_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, L, box_of, box);
+    }
+    MC_CK(cudaMemsetAsync(sum, 0, (size_t)P * dim * 8, s));
+    MC_CK(cudaMemsetAsync(count, 0, (size_t)P * 4, s));
+    mc_sum_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, sum, count);
+    mc_palette_kernel<S><<<blocks_of(P * stride), kMcThreads, 0, s>>>(sum, count, P, dim, stride, palette);
+    mc_record_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(sigma, box_of, L, rec);
+    return cudaGetLastError();
+}
+
+size_t median_cut_scratch(int64_t L, int dim, int bits) {
+    const int64_t P = int64_t(1) << bits, half = P / 2;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    return up((size_t)L * 4) + 2 * up((size_t)half * dim * 4) + up((size_t)half * sizeof(McBox)) +
+           up((size_t)half * 256 * 4) + up((size_t)P * dim * 8) + up((size_t)P * 4);
 }
 
 }  // namespace
@@ -121,38 +295,24 @@ void median_cut(int64_t n, int dim, const float *x, int bits, std::vector<int32_
 cudaError_t compress_tree(TreeArrays &a, int bits, const DevAlloc &al, cudaStream_t s) {
     const int64_t L = a.n_leaves, P = int64_t(1) << bits;
     const int dim = 3 * a.K, rs = a.row_stride;
-    std::vector<uint16_t> rows((size_t)L * rs), sig((size_t)L);
-    cudaError_t e = cudaSuccess;
-    if (L > 0) {
-        e = cudaMemcpyAsync(rows.data(), a.sh, (size_t)L * rs * 2, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sig.data(), a.sigma, (size_t)L * 2, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-    }
-    std::vector<float> x((size_t)L * dim);
-    parallel_for(L, [&](int64_t v) {
-        for (int d = 0; d < dim; d++) x[v * dim + d] = bits_to_float(rows[v * rs + d], a.storage);
-    });
-    std::vector<int32_t> index;
-    std::vector<double> pal;
-    median_cut(L, dim, x.data(), bits, index, pal);
-    std::vector<uint16_t> prow((size_t)P * rs, 0);
-    for (int64_t b = 0; b < P; b++)
-        for (int d = 0; d < dim; d++) prow[b * rs + d] = double_to_bits(pal[b * dim + d], a.storage);
-    std::vector<uint32_t> rec((size_t)L);
-    for (int64_t v = 0; v < L; v++) rec[v] = (uint32_t)sig[v] | ((uint32_t)index[v] << 16);
-
     void *palette = al.alloc((size_t)P * rs * 2, s);
     uint32_t *leaf_rec = (uint32_t *)al.alloc((size_t)std::max<int64_t>(L, 1) * 4, s);
-    if (!palette || !leaf_rec) {
-        al.release(palette, s);
-        al.release(leaf_rec, s);
-        return cudaErrorMemoryAllocation;
+    char *scratch = nullptr;
+    cudaError_t e = (palette && leaf_rec) ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&scratch, median_cut_scratch(L, dim, bits), s);
+    if (e == cudaSuccess) {
+        if (a.storage == DOT_STORAGE_F16)
+            e = median_cut<__half>((const __half *)a.sh, (const __half *)a.sigma, L, dim, rs, bits,
+                                   (__half *)palette, leaf_rec, scratch, s);
+        else
+            e = median_cut<__nv_bfloat16>((const __nv_bfloat16 *)a.sh, (const __nv_bfloat16 *)a.sigma,
+                                          L, dim, rs, bits, (__nv_bfloat16 *)palette, leaf_rec,
+                                          scratch, s);
     }
-    e = cudaMemcpyAsync(palette, prow.data(), (size_t)P * rs * 2, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && L > 0)
-        e = cudaMemcpyAsync(leaf_rec, rec.data(), (size_t)L * 4, cudaMemcpyHostToDevice, s);
+    if (scratch) {
+        const cudaError_t ef = cudaFreeAsync(scratch, s);
+        if (e == cudaSuccess) e = ef;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         al.release(palette, s);
