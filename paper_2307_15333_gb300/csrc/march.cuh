@@ -317,8 +317,14 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     constexpr bool SHADE = MODE == kFwd || MODE == kBwd || MODE == kFwdBwd;
     float Y[K];
     if constexpr (SHADE) sh_basis<K>(dw[0], dw[1], dw[2], Y);
-    float4 rec[MODE == kFwdBwd ? 2 * kRecordSegments : 1];  // (leaf, w, Tn, delta), (colour)
+    // POST (small forward and fused launches): the occupied segments are recorded during the march
+    // and shaded after it, in march order, so the lock-step traversal loop carries no shading; the
+    // record holds (row, w, Tn, delta), and for the fused pass also each segment's colour
+    constexpr bool POST = DEFER && (MODE == kFwd || MODE == kFwdBwd);
+    constexpr int RS = MODE == kFwdBwd ? 2 : 1;  // float4 per record entry
+    float4 rec[MODE == kFwdBwd ? 2 * kRecordSegments : (POST ? kRecordSegments : 1)];
     int nrec = 0;
+    int nshaded = 0;  // POST: record entries shaded so far
     float g[3], rgbf[3];
     if constexpr (MODE == kBwd) {
 #pragma unroll
@@ -428,6 +434,24 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
                 }
                 ++nrec;
             }
+        }
+    };
+    // POST: shades record entries [nshaded, upto) in order (their rows were prefetched into L1 when
+    // they were recorded)
+    auto post_shade = [&](int upto) {
+        if constexpr (POST) {
+            for (int i = nshaded; i < upto; i++) {
+                const float4 a = rec[RS * i];
+                float z[3], col[3];
+                leaf_z<S, K, DEFER>(shp + (int64_t)__float_as_int(a.x) * tv.row_stride, Y, z, pol_stream);
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++)
+                    col[ch] = rp.color_act == DOT_ACT_LINEAR ? z[ch] : sigmoid<EXACT>(z[ch]);
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) C[ch] = fmaf(a.y, col[ch], C[ch]);
+                if constexpr (MODE == kFwdBwd) rec[RS * i + 1] = make_float4(col[0], col[1], col[2], 0.f);
+            }
+            nshaded = upto > nshaded ? upto : nshaded;
         }
     };
     int32_t p_leaf = -1;  // deferred occupied segment (DEFER)
@@ -561,7 +585,16 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             const float alpha = 1.f - e;
             const float w = T * alpha;
             if constexpr (SHADE) {
-                if constexpr (DEFER) {
+                if constexpr (POST) {
+                    if (nrec < kRecordSegments) {
+                        prefetch_row<S, K>(shp + row * tv.row_stride);
+                        rec[RS * nrec] = make_float4(__int_as_float((int32_t)row), w, T * e, delta);
+                        ++nrec;
+                    } else {  // record full: shade it now, in order, then this segment in place
+                        if (nshaded < kRecordSegments) post_shade(kRecordSegments);
+                        shade(leaf, row, w, T * e, delta);
+                    }
+                } else if constexpr (DEFER) {
                     prefetch_row<S, K>(shp + row * tv.row_stride);
                     if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
                     p_leaf = leaf;
@@ -586,7 +619,9 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         leaf = next_leaf;
         level = next_level;
     }
-    if constexpr (DEFER && SHADE) {
+    if constexpr (POST) {
+        post_shade(nrec < kRecordSegments ? nrec : kRecordSegments);
+    } else if constexpr (DEFER && SHADE) {
         if (p_leaf >= 0) shade(p_leaf, p_row, p_w, p_Tn, p_delta);
     }
 #pragma unroll
