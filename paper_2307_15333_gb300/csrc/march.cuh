@@ -317,10 +317,12 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
     constexpr bool SHADE = MODE == kFwd || MODE == kBwd || MODE == kFwdBwd;
     float Y[K];
     if constexpr (SHADE) sh_basis<K>(dw[0], dw[1], dw[2], Y);
-    // POST (small forward and fused launches): the occupied segments are recorded during the march
-    // and shaded after it, in march order, so the lock-step traversal loop carries no shading; the
-    // record holds (row, w, Tn, delta), and for the fused pass also each segment's colour
-    constexpr bool POST = DEFER && (MODE == kFwd || MODE == kFwdBwd);
+    // POST (small forward and fused launches, SH degree 2 and 3): the occupied segments are
+    // recorded during the march and shaded after it, in march order, so the lock-step traversal
+    // loop carries no shading; the record holds (row, w, Tn, delta), and for the fused pass also
+    // each segment's colour.  Rows of degree 0 and 1 are cheap enough to shade in the loop (the
+    // tiny degree-1 scene's 2^16-ray fused pass: 36.97 us with the record, 32.85 us without)
+    constexpr bool POST = DEFER && (MODE == kFwd || MODE == kFwdBwd) && K >= 9;
     constexpr int RS = MODE == kFwdBwd ? 2 : 1;  // float4 per record entry
     float4 rec[MODE == kFwdBwd ? 2 * kRecordSegments : (POST ? kRecordSegments : 1)];
     int nrec = 0;
