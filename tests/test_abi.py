@@ -86,3 +86,16 @@ def test_render_views_host_workspace_sizes():
     assert f(0, 800, 800) == 0
     for bad in ((-1, 8, 8), (65536, 8, 8), (1, 0, 8), (1, 8, 65537)):
         assert f(*bad, 0) == -1
+
+
+def test_probe_argument_errors():
+    """The L2 read-bandwidth probe checks its buffer, size and pass count on the host."""
+    import ctypes as C
+    from paper_2307_15333_gb300 import dot
+    L = dot.lib()
+    assert L.dot_probe_l2_read(None, 1024, 1, None, None) == dot.DOT_ERR_INVALID_ARG
+    buf = C.create_string_buffer(64)
+    aligned = (C.addressof(buf) + 15) & ~15
+    assert L.dot_probe_l2_read(C.c_void_p(aligned), 24, 1, None, None) == dot.DOT_ERR_INVALID_ARG
+    assert L.dot_probe_l2_read(C.c_void_p(aligned + 4), 16, 1, None, None) == dot.DOT_ERR_INVALID_ARG
+    assert L.dot_probe_l2_read(C.c_void_p(aligned), 16, 0, None, None) == dot.DOT_ERR_INVALID_ARG
