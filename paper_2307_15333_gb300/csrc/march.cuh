@@ -208,6 +208,7 @@ struct RayAxes {
     // direction, so that axis never exits; inv16 > 0 when the exit face is the upper one); grid
     // position at t: t dn16 + on16
     float inv16[3], c16[3], on16[3], dn16[3];
+    int upm[3];              // fast mode: -1 where the exit face is the upper one, else 0
     float ow[3], dw[3], invw[3], lo[3], size;  // exact mode
 };
 
@@ -270,6 +271,7 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             r.c16[a] = r.sg[a] != 0 ? -r.on[a] * inv : pinf<float>();
             r.on16[a] = r.on[a] * 65536.f;
             r.dn16[a] = r.dn[a] * 65536.f;
+            r.upm[a] = r.sg[a] > 0 ? -1 : 0;
         } else {
             r.ow[a] = ow[a];
             r.dw[a] = dw[a];
@@ -357,15 +359,17 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         pol_stream = l2_policy_first();
     }
 
-    // descend from (node, level) to the leaf holding gc
+    // descend from (node, level) to the leaf holding gc.  Table indices fit 32 bits: a tree holds
+    // at most 2^27 leaves (the rope encoding) and fewer than 2^28 nodes (import checks the child
+    // table), so leaf * 6 + face and node * 8 + slot are formed in 32-bit arithmetic.
     auto descend = [&](int32_t node, int level, int32_t &leaf_out, int &level_out) -> bool {
         int32_t c;
         const int g0 = gc[0] << 2, g1 = gc[1] << 1, g2 = gc[2];  // slot bits land at 4, 2, 1
         while (true) {
             const int sh = kGridBits - 1 - level;
             const int j = ((g0 >> sh) & 4) | ((g1 >> sh) & 2) | ((g2 >> sh) & 1);
-            if constexpr (DEFER) c = ld_hint(tv.child + (int64_t)node * 8 + j, pol_keep);
-            else c = __ldg(tv.child + (int64_t)node * 8 + j);
+            if constexpr (DEFER) c = ld_hint(tv.child + (uint32_t)(node * 8 + j), pol_keep);
+            else c = __ldg(tv.child + (uint32_t)(node * 8 + j));
             ++level;
             if constexpr (MODE == kStats) out.st[3] += 1;
             if (c < 0 || level >= tv.max_level) break;
@@ -491,17 +495,18 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             row = leaf;
         }
         const int cs = 1 << (kGridBits - level);
-        int lo_g[3];
+        int lo_g[3], bnd[3];
         PT te[3];
         PT tout = pinf<PT>();
         bool outside = false;
         if constexpr (!EXACT) {
             // exit: the nearest of the three faces ahead (a zero direction gives +inf)
-            const int msk = ~(cs - 1);
+            const int msk = -cs;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 lo_g[a] = gc[a] & msk;
-                te[a] = fmaf((float)(r.inv16[a] > 0.f ? lo_g[a] + cs : lo_g[a]), r.inv16[a], r.c16[a]);
+                bnd[a] = lo_g[a] + (cs & r.upm[a]);  // the exit plane on this axis
+                te[a] = fmaf((float)bnd[a], r.inv16[a], r.c16[a]);
             }
             tout = fminf(fminf(te[0], te[1]), te[2]);
         } else {
@@ -526,17 +531,16 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
         if constexpr (!EXACT) {
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                if (te[a] == tout) {  // step across every face hit at tout
-                    const bool up = r.inv16[a] > 0.f;
-                    gc[a] = up ? lo_g[a] + cs : lo_g[a] - 1;
-                    outside |= (unsigned)gc[a] > 65535u;
-                    ++crossed;
-                    face = 2 * a + (up ? 1 : 0);
-                } else {              // the exit point, clamped into the old cell
-                    const int gi = (int)floorf(fmaf(toutv, r.dn16[a], r.on16[a]));
-                    gc[a] = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
-                }
+                // across every face hit at tout (the plane itself upwards, the cell below it
+                // downwards); on the other axes the exit point, clamped into the old cell
+                const bool x = te[a] == tout;
+                const int gi = (int)floorf(fmaf(toutv, r.dn16[a], r.on16[a]));
+                const int in = min(max(gi, lo_g[a]), lo_g[a] + cs - 1);
+                gc[a] = x ? bnd[a] + ~r.upm[a] : in;
+                crossed += x ? 1 : 0;
+                face = x ? 2 * a + (r.upm[a] & 1) : face;
             }
+            outside = ((gc[0] | gc[1] | gc[2]) & ~65535) != 0;
         } else {
 #pragma unroll
             for (int a = 0; a < 3; a++) {
@@ -558,8 +562,8 @@ __device__ __forceinline__ void march_ray(const TreeView &tv, const RenderParams
             bool found;
             if (crossed == 1) {  // across one face: its rope
                 int32_t rp;
-                if constexpr (DEFER) rp = ld_hint(tv.rope + (int64_t)leaf * 6 + face, pol_keep);
-                else rp = __ldg(tv.rope + (int64_t)leaf * 6 + face);
+                if constexpr (DEFER) rp = ld_hint(tv.rope + (uint32_t)(leaf * 6 + face), pol_keep);
+                else rp = __ldg(tv.rope + (uint32_t)(leaf * 6 + face));
                 if constexpr (MODE == kStats) out.st[3] += 1;
                 if (rp >= 0) {  // the node at this leaf's level: descend into the finer neighbour
                     found = rp < tv.n_nodes && descend(rp, level, next_leaf, next_level);

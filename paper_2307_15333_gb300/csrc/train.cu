@@ -311,8 +311,10 @@ __device__ __forceinline__ float rho_pow(float rho, int k) {
 
 // G lanes per touched leaf: lane 0 updates the density, the lanes walk the coefficient row four
 // at a time (16-byte gradient and mean-square loads, coalesced across the lanes).  A group takes U
-// leaves of the list per pass and issues all their loads before any update, so U leaves share
-// one memory round trip.
+// leaves of the list per pass.  Each pass issues all its loads (the leaves' last-update steps,
+// densities and first row chunks) before any arithmetic, and the list entries of the next pass
+// are loaded one pass ahead, so a pass costs one memory round trip instead of three (list, then
+// last step, then the rows behind the decay's loop).
 template <typename S, bool VEC, int G, int U>
 __global__ void __launch_bounds__(kTrainThreads, DOT_SPARSE_MINB)
 rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
@@ -323,26 +325,30 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
                       float lr_sigma, float lr_sh, Rms o) {
     static_assert(G == 4 || G == 8 || G == 16, "group of 4, 8 or 16 lanes");
     constexpr int LOG_G = G == 4 ? 2 : (G == 8 ? 3 : 4);
+    using V = Vec4<S>;
     const int64_t n = *count;
     const int gl = threadIdx.x & (G - 1);
     const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> LOG_G;
-    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> LOG_G; i0 < n;
-         i0 += groups * U) {
-        int32_t v[U];
+    const int64_t per_pass = groups * U;
+    const int q4 = width / 4;
+    int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> LOG_G;
+    int32_t vn[U];  // list entries of the next pass
+#pragma unroll
+    for (int u = 0; u < U; u++) vn[u] = i0 + u * groups < n ? list[i0 + u * groups] : 0;
+    for (; i0 < n; i0 += per_pass) {
+        int32_t v[U], lv[U];
         bool ok[U];
-        float decay[U];
+        float ps[U], gs[U], ms[U];
+        float4 g[U], m[U];
+        typename V::T pv[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             ok[u] = i0 + u * groups < n;
-            v[u] = ok[u] ? list[i0 + u * groups] : 0;
+            v[u] = vn[u];
+            lv[u] = ok[u] ? last[v[u]] : step - 1;
         }
-#pragma unroll
-        for (int u = 0; u < U; u++)
-            decay[u] = ok[u] ? rho_pow(o.rho, step - last[v[u]] - 1) : 0.f;  // steps sat out
         if (gl == 0) {
-            o.lr = lr_sigma;
-            float ps[U], gs[U], ms[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (ok[u]) {
@@ -351,12 +357,41 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
                     ms[u] = ms_sigma[v[u]];
                 }
             }
+        }
+        auto load_chunk = [&](int q) {  // four coefficients of every leaf of the pass
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (ok[u]) {
-                    float m = decay[u] * ms[u];
-                    const float p = rms_update(ps[u], gs[u], m, o);
-                    ms_sigma[v[u]] = m;
+#if DOT_SPARSE_STREAM
+                    g[u] = __ldcs(reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width) + q);
+                    m[u] = __ldcs(reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width) + q);
+#else
+                    g[u] = reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width)[q];
+                    m[u] = reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width)[q];
+#endif
+                    pv[u] = *reinterpret_cast<const typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q);
+                }
+            }
+        };
+        if constexpr (VEC) {
+            if (gl < q4) load_chunk(gl);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t j = i0 + per_pass + u * groups;
+            vn[u] = j < n ? list[j] : 0;
+        }
+        float decay[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) decay[u] = ok[u] ? rho_pow(o.rho, step - lv[u] - 1) : 0.f;  // steps sat out
+        if (gl == 0) {
+            o.lr = lr_sigma;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (ok[u]) {
+                    float mm = decay[u] * ms[u];
+                    const float p = rms_update(ps[u], gs[u], mm, o);
+                    ms_sigma[v[u]] = mm;
                     sigma[v[u]] = Storage<S>::from_f32(p);
                     if (o.zero_grad) grad_sigma[v[u]] = 0.f;
                 }
@@ -364,24 +399,8 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
         }
         o.lr = lr_sh;
         if constexpr (VEC) {
-            using V = Vec4<S>;
-            const int q4 = width / 4;
             for (int q = gl; q < q4; q += G) {
-                float4 g[U], m[U];
-                typename V::T pv[U];
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    if (ok[u]) {
-#if DOT_SPARSE_STREAM
-                        g[u] = __ldcs(reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width) + q);
-                        m[u] = __ldcs(reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width) + q);
-#else
-                        g[u] = reinterpret_cast<const float4 *>(grad_sh + (int64_t)v[u] * width)[q];
-                        m[u] = reinterpret_cast<const float4 *>(ms_sh + (int64_t)v[u] * width)[q];
-#endif
-                        pv[u] = *reinterpret_cast<const typename V::T *>(sh + (int64_t)v[u] * row_stride + 4 * q);
-                    }
-                }
+                if (q != gl) load_chunk(q);
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     if (!ok[u]) continue;
@@ -416,14 +435,14 @@ rmsprop_sparse_kernel(const int32_t *__restrict__ list, const int32_t *__restric
             for (int u = 0; u < U; u++) {
                 if (!ok[u]) continue;
                 for (int c = gl; c < width; c += G) {
-                    float *g = grad_sh + (int64_t)v[u] * width + c;
-                    float *ms = ms_sh + (int64_t)v[u] * width + c;
+                    float *gp = grad_sh + (int64_t)v[u] * width + c;
+                    float *mp = ms_sh + (int64_t)v[u] * width + c;
                     S *pp = sh + (int64_t)v[u] * row_stride + c;
-                    float m = decay[u] * *ms;
-                    const float p = rms_update(Storage<S>::to_f32(*pp), *g, m, o);
-                    *ms = m;
+                    float mm = decay[u] * *mp;
+                    const float p = rms_update(Storage<S>::to_f32(*pp), *gp, mm, o);
+                    *mp = mm;
                     *pp = Storage<S>::from_f32(p);
-                    if (o.zero_grad) *g = 0.f;
+                    if (o.zero_grad) *gp = 0.f;
                 }
             }
         }
