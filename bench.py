@@ -407,7 +407,7 @@ def measure_l2_read(local: int):
 
 
 def two_level(compulsory_bytes, sample_bytes, t_meas_s, hbm_gbs, l2_gbs):
-    """Survey's roofline: t_roof = max(compulsory / HBM bandwidth, sample / L2 bandwidth)."""
+    """Two-level roofline: t_roof = max(compulsory / HBM bandwidth, sample / L2 bandwidth)."""
     t_hbm = compulsory_bytes / (hbm_gbs * 1e9)
     t_l2 = sample_bytes / (l2_gbs * 1e9)
     t_roof = max(t_hbm, t_l2)
@@ -526,10 +526,11 @@ def timed(fn, n, stream):
 
 def measure_training(scene, cams, steps: int):
     """Algorithm 1 on the NeRF-synthetic-shaped scene: optimisation steps on 2^16-ray batches
-    (forward with the fused SUM_ALPHA signal, MSE gradient, backward, RMSProp of every leaf fused
-    with zeroing the gradients) against targets rendered from a seeded perturbed copy of the tree
-    (same cells, other seed), then one refine (recursive pruning at the 20th-percentile signal,
-    sampling of the top 5%)."""
+    (one fused launch of the forward with the SUM_ALPHA signal, the MSE gradient and the backward
+    with touched-leaf flags, then RMSProp of the touched leaves with their gradients zeroed and the
+    decay of the others deferred) against targets rendered from a copy of the tree with other
+    seeded parameters (same cells, other seed), then one refine (recursive pruning at the
+    20th-percentile signal, sampling of the top 5%)."""
     import dataclasses
 
     import torch
@@ -1048,7 +1049,7 @@ def run_dot(args):
                 "+ 12 B per ray",
         "t_at_peak_ms": compulsory / (hbm * 1e9) * 1e3, "t_meas_ms": mean_launch_s * 1e3}
 
-    # the survey's two-level roofline with a measured L2 read bandwidth
+    # the two-level roofline with a measured L2 read bandwidth
     if rank == 0:
         l2 = measure_l2_read(local)
         comp_fused = u_occ_b16 * (P + 2 * grad_bytes_per_occupied(K)) + BATCH * 36
