@@ -18,11 +18,10 @@ def render_views(tree: dot.Octree, cams_host: torch.Tensor, width: int, height: 
     given), through dot_render_views_host: into page-locked host images (the default here) one
     launch writes every image in place; into other host buffers the views are rendered in chunks
     and each finished chunk is copied to the host while the next ones render.  With `view_order`
-    the views are
-    rendered in a nearest-neighbour chain (dot_camera_order) so that consecutive views reuse
-    the leaves in L2; the images do not change.  Pass a device `workspace` (uint8, at least
-    dot_render_views_host_workspace bytes) to reuse one across calls.  The call returns after the
-    images have arrived."""
+    the views are rendered in a nearest-neighbour chain (dot_camera_order) so that consecutive
+    views reuse the leaves in L2; the images do not change.  Pass a device `workspace` (uint8, at
+    least dot_render_views_host_workspace bytes) to reuse one across calls.  The call returns
+    after the images have arrived."""
     if opts is None:
         opts = dot.render_opts()
     n = cams_host.shape[0]
