@@ -7,7 +7,6 @@ library cannot be loaded the import fails; there is no fallback.
 from __future__ import annotations
 
 import ctypes
-import os
 from typing import Optional, Sequence
 
 import numpy as np
