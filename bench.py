@@ -750,6 +750,16 @@ def measure_tanks_temples(steps: int):
                 fpairs, stream)
     del gfull
     f_pair = ab + alg_bytes_bwd(st, R, 2, K)
+    # distinct occupied leaves the 311 M rays touch (a max-weight signal pass, not timed): the
+    # compulsory bytes of the forward and of a forward + backward pair over all views
+    touched = torch.zeros(L, dtype=torch.float32, device="cuda")
+    dot.dot_accumulate_signal(tree, rays, opts, dot.dot.DOT_SIGNAL_MAX_WEIGHT, touched)
+    u_leaf = int(torch.count_nonzero(touched))
+    del touched
+    n_empty = int((tree.sigma <= 0).sum())
+    P = 2 * (1 + 3 * K)
+    comp_fwd = u_leaf * P + tree.n_nodes * 32 + n_empty * 2 + R * 12
+    comp_pair = 2 * comp_fwd + u_leaf * 2 * grad_bytes_per_occupied(K) + R * 12
     out = {"workload": "tanks_temples_d10_sh3_bf16_150x1920x1080", "leaves": L,
            "nodes": tree.n_nodes, "rays_per_step": R,
            "fwd": {"value": R * n / (ms / 1e3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms / n,
@@ -762,7 +772,9 @@ def measure_tanks_temples(steps: int):
            "fwd_bwd_full_batch": {"value": R * fpairs / (fms / 1e3) / 1e6, "unit": "Mrays/s",
                                   "batch_rays": R, "ms_per_pair": fms / fpairs,
                                   "alg_bytes_per_pair": f_pair,
-                                  "roofline_frac": f_pair / (fms / fpairs / 1e3) / 1e9 / hbm}}
+                                  "roofline_frac": f_pair / (fms / fpairs / 1e3) / 1e9 / hbm},
+           "compulsory": {"occupied_leaves_touched": u_leaf, "fwd_bytes": comp_fwd,
+                          "pair_bytes": comp_pair}}
     tree.free()
     return out
 
@@ -1060,6 +1072,23 @@ def run_dot(args):
                                         l2["l2_read_gbs"]),
             "fused_compulsory": "distinct occupied leaves of the batch x (payload + FP32 gradient "
                                 "read and write) + 36 B per ray"}
+        # forward + backward over all 64 M rays: each pass reads what a forward must, and the
+        # backward also reads and writes the touched leaves' FP32 gradients and reads dL/dC
+        comp_pair = 2 * compulsory + u_leaf * 2 * grad_bytes_per_occupied(K) + R * 12
+        fb = fwd_bwd["full_batch"]
+        roofline["two_level"]["fwd_bwd_full_batch"] = two_level(
+            comp_pair, fb["alg_bytes_per_pair"], fb["ms_per_pair"] / 1e3, hbm, l2["l2_read_gbs"])
+        roofline["two_level"]["pair_compulsory"] = (
+            "2 x the forward's compulsory bytes + the touched leaves' FP32 gradients read and "
+            "written + 12 B of dL/dC per ray")
+        if tt_res is not None:
+            c = tt_res["compulsory"]
+            tt_res["fwd"]["two_level"] = two_level(
+                c["fwd_bytes"], tt_res["fwd"]["alg_bytes_per_launch"],
+                tt_res["fwd"]["ms_per_step"] / 1e3, hbm, l2["l2_read_gbs"])
+            tb = tt_res["fwd_bwd_full_batch"]
+            tb["two_level"] = two_level(c["pair_bytes"], tb["alg_bytes_per_pair"],
+                                        tb["ms_per_pair"] / 1e3, hbm, l2["l2_read_gbs"])
 
     cpu, parity = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
