@@ -105,6 +105,60 @@ def test_edge_cases():
     tree.free()
 
 
+def _edge_rays(t, s64, lo, size, n_leaves=4):
+    """Rays that miss the root, start inside it, run along root edges and faces, and, for a few
+    occupied leaves: along the leaf's edge (two exit planes tied all the way), along one of its
+    faces and through its centre on each axis, and through its corner on the two diagonals
+    (three planes tied at every lattice corner)."""
+    o = [[3, 3, 3], [0, 0, 0], [0.1, -0.2, 0.3], [-1.0, -1.0, 5.0], [0.03125, 0.0, 0.0],
+         [-1.0, 0.1, 5.0], [1.0, 0.2, -5.0]]
+    d = [[1, 0, 0], [0, 0, 1], [0.6, 0.0, -0.8], [0, 0, -1], [0, 1, 0], [0, 0, -1], [0, 0, 1]]
+    keys = np.asarray(t["leaf_key"], np.uint64)
+    occ = np.nonzero(s64 > 0)[0]
+    for v in occ[:: max(1, len(occ) // n_leaves)][:n_leaves]:
+        k = int(keys[v])
+        lv = (k.bit_length() - 1) // 3
+        c = [0, 0, 0]
+        for i in range(lv):
+            tri = (k >> (3 * (lv - 1 - i))) & 7
+            c = [(c[0] << 1) | (tri >> 2), (c[1] << 1) | ((tri >> 1) & 1), (c[2] << 1) | (tri & 1)]
+        cs = size / (1 << lv)
+        x0, y0, z0 = (lo[a] + c[a] * cs for a in range(3))
+        xc, yc, zc = x0 + cs / 2, y0 + cs / 2, z0 + cs / 2
+        o += [[x0, y0, 5.0], [-5.0, y0, zc], [xc, 5.0, zc], [xc, yc, -5.0],
+              [x0 - 3.0, y0 - 3.0, z0 - 3.0], [x0 + 3.0, y0 + 3.0, z0 - 3.0]]
+        d += [[0, 0, -1], [1, 0, 0], [0, -1, 0], [0, 0, 1], [1, 1, 1], [-1, -1, 1]]
+    o = np.array(o, np.float32)
+    d = np.array(d, np.float32)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o, d
+
+
+@pytest.mark.parametrize("storage", [si.STORAGE_F32, si.STORAGE_F16])
+def test_fast_path_edge_cases(storage):
+    """The fast (float32 plane time) march on the edge-case rays, in a small launch and in the
+    large-launch build (the rays tiled past two full waves): both match the oracle at the
+    fast-mode tolerance and equal each other bit for bit."""
+    import paper_2307_15333_gb300 as dot
+    scene = si.random_scene(5, max_depth=5, sh_degree=3, storage=storage)
+    tree = dot.octree_from_scene(scene)
+    t, _, _, s64, h64 = oracle_side(scene)
+    lo, size = oracle.root_of(scene)
+    o, d = _edge_rays(t, s64, lo, size)
+    small, Ts = _gpu_render(tree, o, d, background=(0.3, 0.6, 0.9), precision=1)
+    ref, Tr, _ = oracle.render(t, lo, size, s64, h64, 3, o, d, bg=(0.3, 0.6, 0.9))
+    np.testing.assert_array_equal(small[0], np.float32([0.3, 0.6, 0.9]))
+    assert_pixels_close(small, ref, storage, exact=False)
+    assert_pixels_close(Ts, Tr, storage, exact=False, what="T")
+    reps = (2 * 1024 * 152) // o.shape[0] + 1
+    big, Tb = _gpu_render(tree, np.tile(o, (reps, 1)), np.tile(d, (reps, 1)),
+                          background=(0.3, 0.6, 0.9), precision=1)
+    assert np.array_equal(big, np.tile(small, (reps, 1))), "large launch differs from small"
+    assert np.array_equal(Tb, np.tile(Ts, reps)), "large launch T differs from small"
+    assert tree.status() == 0
+    tree.free()
+
+
 def test_full_size_nerf_synthetic_sampled_pixels():
     """Config at full size (2.9M leaves, 800x800 views) in the bench's launch configuration
     (camera mode, all views in one launch, nearest-neighbour view order); sampled pixels against
