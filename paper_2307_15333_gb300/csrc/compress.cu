@@ -12,7 +12,8 @@
 //
 // On the GPU every leaf carries its box number; no member lists are kept.  A round:
 //   1. per box and axis, the min and max of the members (order-preserving 32-bit keys, atomics
-//      aggregated over the lanes of a warp that share a box), and the member count;
+//      aggregated over the lanes of a warp that share a box, and in the first rounds, with few
+//      boxes, over a block in shared memory), and the member count;
 //   2. per box, the longest axis;
 //   3. per box, the member of rank floor(m/2) in (value, id) order: a radix select over the
 //      64-bit keys (value key << 32 | leaf id), unique per leaf, in 8 histogram passes of 8 bits;
@@ -81,6 +82,52 @@ mc_minmax_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
             atomicMax(hi + (int64_t)b * dim + d, kmax);
         }
     }
+}
+
+// The same for rounds of at most kMcSharedBoxes boxes, where every box has tens of thousands of
+// members and the atomics above would queue on a few addresses: a resident grid walks the leaves,
+// each block keeps its min / max per (box, axis) and its member counts in shared memory (only its
+// own lanes contend there, after the warp's aggregation), then adds them to the global ones with
+// one atomic per (box, axis).  Min and max are exact in any order, so the result is the same.
+constexpr int kMcSharedBoxes = 64;
+constexpr int kMcMaxDim = 48;  // 3 x 16 coefficients at SH degree 3
+template <typename S>
+__global__ void __launch_bounds__(kMcThreads)
+mc_minmax_shared_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
+                        const int32_t *__restrict__ box_of, unsigned *lo, unsigned *hi, McBox *box,
+                        int nb) {
+    __shared__ unsigned s_lo[kMcSharedBoxes * kMcMaxDim], s_hi[kMcSharedBoxes * kMcMaxDim];
+    __shared__ int s_cnt[kMcSharedBoxes];
+    const int n = nb * dim;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        s_lo[i] = 0xffffffffu;
+        s_hi[i] = 0u;
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < L; b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = b0 + threadIdx.x;
+        const bool ok = v < L;
+        const int b = ok ? box_of[v] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        const bool leader = (threadIdx.x & 31) == (__ffs(grp) - 1);
+        if (ok && leader) atomicAdd(&s_cnt[b], __popc(grp));
+        for (int d = 0; d < dim; d++) {
+            const unsigned k = ok ? mc_key(mc_coef(rows, v, stride, d)) : 0u;
+            const unsigned kmin = __reduce_min_sync(grp, k), kmax = __reduce_max_sync(grp, k);
+            if (ok && leader) {
+                atomicMin(&s_lo[b * dim + d], kmin);
+                atomicMax(&s_hi[b * dim + d], kmax);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (s_lo[i] != 0xffffffffu) atomicMin(lo + i, s_lo[i]);
+        if (s_hi[i] != 0u) atomicMax(hi + i, s_hi[i]);
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(&box[i].count, s_cnt[i]);
 }
 
 // longest axis of every box; the radix select starts at rank floor(m/2) + 1 (1-based)
@@ -262,12 +309,22 @@ cudaError_t median_cut(const S *rows, const S *sigma, int64_t L, int dim, int st
     int32_t *count = reinterpret_cast<int32_t *>(scratch + off);
 
     if (L == 0) return cudaMemsetAsync(palette, 0, (size_t)P * stride * sizeof(S), s);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     MC_CK(cudaMemsetAsync(hist, 0, (size_t)half * 256 * 4, s));
     mc_init_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(box_of, L);
     for (int r = 0; r < bits; r++) {
         const int64_t nb = int64_t(1) << r;
         mc_clear_kernel<<<blocks_of(nb * dim), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
-        mc_minmax_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo, hi, box);
+        if (nb <= kMcSharedBoxes && dim <= kMcMaxDim) {
+            const unsigned grid = std::min<unsigned>(blocks_of(L), (unsigned)(4 * sms));
+            mc_minmax_shared_kernel<S><<<grid, kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo,
+                                                                   hi, box, (int)nb);
+        } else {
+            mc_minmax_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo,
+                                                                    hi, box);
+        }
         mc_axis_kernel<<<blocks_of(nb), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
         for (int shift = 56; shift >= 0; shift -= 8) {
             mc_hist_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, L, box_of, box, shift, hist);
