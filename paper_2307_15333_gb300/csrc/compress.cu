@@ -10,7 +10,8 @@
 // to child 2b + 1 (a box of fewer than two keeps its members in child 2b); a palette row is the
 // mean of its box (zeros if empty), rounded to the storage type.
 //
-// On the GPU every leaf carries its box number; no member lists are kept.  A round:
+// On the GPU every leaf carries its box number, and a permutation of the leaves keeps every box's
+// members contiguous (split stably after each round).  A round:
 //   1. per box and axis, the min and max of the members (order-preserving 32-bit keys, atomics
 //      aggregated over the lanes of a warp that share a box, and in the first rounds, with few
 //      boxes, over a block in shared memory), and the member count;
@@ -67,9 +68,11 @@ __global__ void mc_clear_kernel(unsigned *lo, unsigned *hi, McBox *box, int64_t 
 template <typename S>
 __global__ void __launch_bounds__(kMcThreads)
 mc_minmax_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
-                 const int32_t *__restrict__ box_of, unsigned *lo, unsigned *hi, McBox *box) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool ok = v < L;
+                 const int32_t *__restrict__ box_of, const int32_t *__restrict__ perm, unsigned *lo,
+                 unsigned *hi, McBox *box) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = i < L;
+    const int64_t v = ok ? perm[i] : 0;
     const int b = ok ? box_of[v] : -1;
     const unsigned grp = __match_any_sync(0xffffffffu, b);
     const bool leader = (threadIdx.x & 31) == (__ffs(grp) - 1);
@@ -94,8 +97,8 @@ constexpr int kMcMaxDim = 48;  // 3 x 16 coefficients at SH degree 3
 template <typename S>
 __global__ void __launch_bounds__(kMcThreads)
 mc_minmax_shared_kernel(const S *__restrict__ rows, int stride, int dim, int64_t L,
-                        const int32_t *__restrict__ box_of, unsigned *lo, unsigned *hi, McBox *box,
-                        int nb) {
+                        const int32_t *__restrict__ box_of, const int32_t *__restrict__ perm,
+                        unsigned *lo, unsigned *hi, McBox *box, int nb) {
     __shared__ unsigned s_lo[kMcSharedBoxes * kMcMaxDim], s_hi[kMcSharedBoxes * kMcMaxDim];
     __shared__ int s_cnt[kMcSharedBoxes];
     const int n = nb * dim;
@@ -106,8 +109,9 @@ mc_minmax_shared_kernel(const S *__restrict__ rows, int stride, int dim, int64_t
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < L; b0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = b0 + threadIdx.x;
-        const bool ok = v < L;
+        const int64_t i = b0 + threadIdx.x;
+        const bool ok = i < L;
+        const int64_t v = ok ? perm[i] : 0;
         const int b = ok ? box_of[v] : -1;
         const unsigned grp = __match_any_sync(0xffffffffu, b);
         const bool leader = (threadIdx.x & 31) == (__ffs(grp) - 1);
@@ -239,9 +243,47 @@ __global__ void mc_assign_kernel(const S *__restrict__ rows, int stride, int64_t
     box_of[v] = child;
 }
 
-__global__ void mc_init_kernel(int32_t *box_of, int64_t L) {
+__global__ void mc_init_kernel(int32_t *box_of, int32_t *perm, int64_t L) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < L) box_of[v] = 0;
+    if (v < L) {
+        box_of[v] = 0;
+        perm[v] = (int32_t)v;
+    }
+}
+
+// The members of every box are kept contiguous in perm (box b at [start[b], start[b] + m_b)), so
+// that the min / max pass meets each box's members together and a warp's lanes mostly share one
+// box.  After a round's assignment each segment is split, stably, into its child 2b (the first
+// lower(m_b) entries) and 2b + 1; up[i] flags the entries that moved to the upper child and its
+// exclusive scan ranks them within their segment.
+__device__ __forceinline__ int64_t mc_lower(const McBox &x) {
+    return x.count < 2 ? x.count : x.count / 2;
+}
+__global__ void mc_flag_kernel(const int32_t *__restrict__ perm, const int32_t *__restrict__ box_of,
+                               int64_t L, int32_t *__restrict__ up) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L) up[i] = box_of[perm[i]] & 1;
+}
+__global__ void mc_partition_kernel(const int32_t *__restrict__ perm, const int32_t *__restrict__ box_of,
+                                    const int32_t *__restrict__ up_before,
+                                    const int32_t *__restrict__ start, const McBox *__restrict__ box,
+                                    int64_t L, int32_t *__restrict__ perm_next) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int32_t v = perm[i];
+    const int c = box_of[v];
+    const int b = c >> 1;
+    const int64_t s0 = start[b];
+    const int64_t ups = up_before[i] - up_before[s0];  // entries of the segment before i that went up
+    const int64_t pos = (c & 1) ? s0 + mc_lower(box[b]) + ups : s0 + (i - s0) - ups;
+    if (pos >= 0 && pos < L) perm_next[pos] = v;
+}
+__global__ void mc_starts_kernel(const int32_t *__restrict__ start, const McBox *__restrict__ box,
+                                 int64_t n_boxes, int32_t *__restrict__ start_next) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_boxes) return;
+    start_next[2 * b] = start[b];
+    start_next[2 * b + 1] = (int32_t)(start[b] + mc_lower(box[b]));
 }
 
 // FP64 sums of every final box's members, and their counts
@@ -307,23 +349,40 @@ cudaError_t median_cut(const S *rows, const S *sigma, int64_t L, int dim, int st
     double *sum = reinterpret_cast<double *>(scratch + off);
     off += up((size_t)P * dim * 8);
     int32_t *count = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)P * 4);
+    int32_t *perm = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)L * 4);
+    int32_t *perm2 = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)L * 4);
+    int32_t *upf = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)L * 4);
+    int32_t *upscan = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)L * 4);
+    int32_t *start = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)P * 4);
+    int32_t *start2 = reinterpret_cast<int32_t *>(scratch + off);
+    off += up((size_t)P * 4);
+    int32_t *total = reinterpret_cast<int32_t *>(scratch + off);
+    off += up(4);
+    void *scan_scr = scratch + off;
 
     if (L == 0) return cudaMemsetAsync(palette, 0, (size_t)P * stride * sizeof(S), s);
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     MC_CK(cudaMemsetAsync(hist, 0, (size_t)half * 256 * 4, s));
-    mc_init_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(box_of, L);
+    mc_init_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(box_of, perm, L);
+    MC_CK(cudaMemsetAsync(start, 0, sizeof(int32_t), s));  // round 0: one box, from entry 0
     for (int r = 0; r < bits; r++) {
         const int64_t nb = int64_t(1) << r;
         mc_clear_kernel<<<blocks_of(nb * dim), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
         if (nb <= kMcSharedBoxes && dim <= kMcMaxDim) {
             const unsigned grid = std::min<unsigned>(blocks_of(L), (unsigned)(4 * sms));
-            mc_minmax_shared_kernel<S><<<grid, kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo,
-                                                                   hi, box, (int)nb);
+            mc_minmax_shared_kernel<S><<<grid, kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, perm,
+                                                                   lo, hi, box, (int)nb);
         } else {
-            mc_minmax_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, lo,
-                                                                    hi, box);
+            mc_minmax_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, dim, L, box_of, perm,
+                                                                    lo, hi, box);
         }
         mc_axis_kernel<<<blocks_of(nb), kMcThreads, 0, s>>>(lo, hi, box, nb, dim);
         for (int shift = 56; shift >= 0; shift -= 8) {
@@ -331,6 +390,15 @@ cudaError_t median_cut(const S *rows, const S *sigma, int64_t L, int dim, int st
             mc_pick_kernel<<<blocks_of(nb * 32), kMcThreads, 0, s>>>(hist, box, nb, shift);
         }
         mc_assign_kernel<S><<<blocks_of(L), kMcThreads, 0, s>>>(rows, stride, L, box_of, box);
+        if (r + 1 < bits) {  // the next round's segments
+            mc_flag_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(perm, box_of, L, upf);
+            MC_CK(scan_exclusive_i32(upf, upscan, L, total, scan_scr, s));
+            mc_partition_kernel<<<blocks_of(L), kMcThreads, 0, s>>>(perm, box_of, upscan, start, box,
+                                                                    L, perm2);
+            mc_starts_kernel<<<blocks_of(nb), kMcThreads, 0, s>>>(start, box, nb, start2);
+            std::swap(perm, perm2);
+            std::swap(start, start2);
+        }
     }
     MC_CK(cudaMemsetAsync(sum, 0, (size_t)P * dim * 8, s));
     MC_CK(cudaMemsetAsync(count, 0, (size_t)P * 4, s));
@@ -344,7 +412,8 @@ size_t median_cut_scratch(int64_t L, int dim, int bits) {
     const int64_t P = int64_t(1) << bits, half = P / 2;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     return up((size_t)L * 4) + 2 * up((size_t)half * dim * 4) + up((size_t)half * sizeof(McBox)) +
-           up((size_t)half * 256 * 4) + up((size_t)P * dim * 8) + up((size_t)P * 4);
+           up((size_t)half * 256 * 4) + up((size_t)P * dim * 8) + up((size_t)P * 4) +
+           4 * up((size_t)L * 4) + 2 * up((size_t)P * 4) + up(4) + scan_scratch_bytes(L);
 }
 
 }  // namespace
