@@ -512,10 +512,12 @@ int dot_rmsprop_flush(dot_tree *tree, float *ms_sigma, float *ms_sh, int32_t *la
  * type.  Each leaf then keeps one 32-bit record, its 16-bit density in the low half and its
  * palette row in the high half, so rendering reads 4 bytes per segment plus a palette row.
  * bits: 1..16; 16-bit storage only (DOT_ERR_UNSUPPORTED for FP32).  The quantiser runs on the
- * GPU (each round: per-box ranges by atomics, the median member by a per-box radix select over
- * (value, leaf id) keys) and the call synchronises the stream.  Afterwards forward renders, signals, statistics and
- * slot tables read the records; dot_render_backward, dot_rmsprop_step, dot_refine_plan and
- * dot_refine_prune return DOT_ERR_UNSUPPORTED; dot_tree_export writes the expanded coefficients.
+ * GPU (each round: per-box ranges by atomics over a permutation that keeps every box's members
+ * contiguous, the median member by a per-box radix select over (value, leaf id) keys, then a
+ * stable split of every box's segment) and the call synchronises the stream.  Afterwards forward
+ * renders, signals, statistics and slot tables read the records; dot_render_backward,
+ * dot_rmsprop_step, dot_refine_plan and dot_refine_prune return DOT_ERR_UNSUPPORTED;
+ * dot_tree_export writes the expanded coefficients.
  */
 int dot_compress_sh(dot_tree *tree, int32_t bits, void *stream);
 
